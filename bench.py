@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 variational-embedding solver (Algorithm 6 of arXiv:2106.02682).
+
+One step = one sweep of the translation-invariant ADMM / projected dual ascent over the whole
+instance (pair pass, rho_0 update, dual updates, block DFT, per-wavevector projection, inverse
+DFT).  Default workload: 1-D transverse-field Ising chain, h = 1, 2-spin clusters (16 x 16 pair
+marginals), 4096 clusters = 4096 wavevectors (8192 spins), float64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                    [--workload NAME] [--impl ours|reference] [--no-ttb]
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank runs its own replica of the
+instance (the sweep has no cross-instance exchange); value = sweeps of all ranks / max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-certified-bound (residual 1e-6) & ADMM iter/s, warm vs plain, 1 GB300"
+UNIT = "iter/s"
+FP64_PEAK_TFLOPS = 1.25        # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2.07 GHz x 2)
+FP32_PEAK_TFLOPS = 80.5        # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tfim1d_L2_N4096")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-ttb", action="store_true", help="skip the time-to-certified-bound runs")
+    ap.add_argument("--ttb-max-iter", type=int, default=60000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ nvidia-smi clock sampling
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2][i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ algorithmic work per stage
+def stage_work(N, D, npass, ncanon):
+    """Algorithmic flops / bytes per launch of each stage (float64 words).
+
+    Projection of a real symmetric D x D matrix: tridiagonalisation 4/3 D^3 + back-transform
+    2 D^3 + reconstruction D^3 = 13/3 D^3 flops (fixed, whatever eigensolver runs); a complex
+    Hermitian one costs 4x that.  The pair pass adds ~60 D^2 elementwise flops per offset.
+    A DFT pass reads and writes N * D^2 / 2 complex words.
+    """
+    P = N - 1
+    fs = 13.0 / 3.0 * D ** 3
+    return {
+        "pair": {"flops": P * (fs + 60 * D * D), "bytes": P * 8 * (6 * D * D + 4 * D)},
+        "xproj": {"flops": ncanon * 4 * fs, "bytes": 2 * N * D * D * 8},
+        "fft_forward": {"bytes": N * D * D * 8 * 2, "flops": 5.0 * N * D * D / 2 * 6},
+        "fft_inverse": {"bytes": N * D * D * 8 * 2, "flops": 5.0 * N * D * D / 2 * 6},
+    }
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_02682_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload, precision):
+    """Per-launch DRAM traffic of `kernel` from the committed ncu summary, if it was taken on
+    the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    rec = data.get(f"{workload}/{precision}/{kernel}")
+    if not rec or rec.get("source_digest") != source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_rate(workload, seconds, max_sweeps=None):
+    import numpy as np  # noqa: F401
+    from oracle import models as mo
+    from oracle import ve_oracle as vo
+    from paper_2106_02682_gb300 import synth
+    w = synth.WORKLOADS[workload]
+    dim = len(w["lattice"])
+    terms = mo.tfim_terms(1.0, w["h"], dim) if w["kind"] == "tfim" else mo.xxz_terms(1.0, w["h"], dim)
+    pb = vo.Problem(mo.cluster_model(w["lattice"], w["cluster"], *terms))
+    st = vo.initial_state(pb)
+    vo.iterate(pb, st)  # warm-up sweep
+    n, t0, c0 = 0, time.perf_counter(), time.process_time()
+    while True:
+        vo.iterate(pb, st)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_sweeps and n >= max_sweeps):
+            break
+    cores = (time.process_time() - c0) / el
+    return n / el, n, el, round(cores, 2)
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import models as mo  # noqa: F401
+    from oracle import ve_oracle as vo
+    from paper_2106_02682_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    dim = len(w["lattice"])
+    terms = (mo.tfim_terms(1.0, w["h"], dim) if w["kind"] == "tfim" else mo.xxz_terms(1.0, w["h"], dim))
+    pb = vo.Problem(mo.cluster_model(w["lattice"], w["cluster"], *terms))
+    st = vo.initial_state(pb)
+    for _ in range(args.warmup):
+        vo.iterate(pb, st)
+    t0, c0 = time.perf_counter(), time.process_time()
+    for _ in range(args.steps):
+        vo.iterate(pb, st)
+    el = time.perf_counter() - t0
+    cores = round((time.process_time() - c0) / el, 2)
+    value = args.steps / el
+    cfg = workload_config(args, pb.N, pb.D)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full sweeps of {args.workload} after "
+                                   f"{args.warmup} warm-up sweeps (numpy float64 oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def workload_config(args, N, D):
+    from paper_2106_02682_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    return {"workload": args.workload, "lattice": list(w["lattice"]), "cluster": list(w["cluster"]),
+            "model": w["kind"], "h": w["h"], "J": 1.0, "clusters": N, "wavevectors": N,
+            "pair_dim": D, "precision": args.precision, "mu": 10.0, "nu": 10.0, "eps": 2.0,
+            "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02682_gb300 import synth, ve
+    w = synth.WORKLOADS[args.workload]
+    dim = len(w["lattice"])
+    ham = ve.ve_ham_tfim(dim, 1.0, w["h"]) if w["kind"] == "tfim" else ve.ve_ham_xxz(dim, 1.0, w["h"])
+    prec = ve.VE_PREC_FP64 if args.precision == "fp64" else ve.VE_PREC_MIXED
+    stream = torch.cuda.Stream()
+    opt = ve.ve_default_options(precision=prec, stream=stream.cuda_stream)
+    h = ve.ve_create(w["lattice"], w["cluster"], ham, opt)
+    N, m, D = ve.ve_dims(h)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {}
+    try:
+        # mixed precision in the timed loop: force the float32 phase by a zero tolerance
+        ve.ve_iterate(h, args.warmup, 0.0)
+        ve.ve_profile(h, 1)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0[k].record(stream)
+            ve.ve_iterate(h, 1, 0.0)
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+        prof = ve.ve_profile_read(h)
+        ve.ve_profile(h, 0)
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.barrier()
+        max_ms = float(t.item())
+        value = world * args.steps / (max_ms / 1e3)
+        status = ve.ve_get_status(h)
+
+        # ---- end to end through the public API with host buffers
+        sb = ve.ve_state_size(h)
+        host = torch.empty(sb // 8, dtype=torch.float64, pin_memory=True).numpy()
+        ve.ve_get_state(h, host)
+        k_e2e = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ve.ve_set_state(h, host)
+            ve.ve_iterate(h, 1, 0.0)
+            ve.ve_get_state(h, host)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": sb,
+               "d2h_bytes_per_step": sb + 48,
+               "how": "per step: ve_set_state from pinned host, ve_iterate(1 sweep) with status "
+                      "read-back, ve_get_state to pinned host; wall clock"}
+
+        # ---- roofline of the dominant kernel, from the live per-stage events
+        ncanon = sum(1 for _ in range(1))  # replaced below
+        ncanon = (N // 2 + 1) if dim == 1 else None
+        if ncanon is None:
+            M0 = w["lattice"][0] // w["cluster"][0]
+            M1 = w["lattice"][1] // w["cluster"][1]
+            ncanon = sum(1 for k0 in range(M0) for k1 in range(M1)
+                         if (k0 * M1 + k1) <= (((-k0) % M0) * M1 + (-k1) % M1))
+        npass = prof["fft_forward"][1] // max(1, prof["pair"][1])
+        work = stage_work(N, D, npass, ncanon)
+        dom = max(prof, key=lambda s: prof[s][0])
+        ms_launch = prof[dom][0] / max(1, prof[dom][1])
+        wk = work.get(dom, {"flops": 0, "bytes": 0})
+        if dom in ("pair", "xproj"):
+            peak = FP64_PEAK_TFLOPS if prec == 0 else FP32_PEAK_TFLOPS
+            achieved = wk["flops"] / (ms_launch * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_source": ("nominal FP64 rate of the part (recipe table), not in "
+                                    "MEASURED_PEAKS.json" if prec == 0 else
+                                    "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2.07 GHz")}
+        else:
+            peak = 6789.6
+            try:
+                with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                    peak = json.load(fh)["hbm_gbs"]
+            except (OSError, ValueError, KeyError):
+                pass
+            achieved = wk["bytes"] / (ms_launch * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        roof["kernel"] = dom
+        roof["ms_per_launch"] = ms_launch
+        roof["traffic"] = ncu_traffic(dom, args.workload, args.precision)
+        roof["algorithmic_per_launch"] = wk
+        stages = {s: {"ms_per_launch": prof[s][0] / max(1, prof[s][1]), "launches": prof[s][1],
+                      "share": prof[s][0] / max(1e-12, sum(v[0] for v in prof.values()))}
+                  for s in prof}
+        launches = int(sum(v[1] for v in prof.values()))
+
+        # ---- time to certified bound, float64 and mixed, fresh handles
+        ttb = None
+        if not args.no_ttb and rank == 0:
+            ttb = {}
+            for pname, pcode in (("fp64", ve.VE_PREC_FP64), ("mixed", ve.VE_PREC_MIXED)):
+                hh = ve.ve_create(w["lattice"], w["cluster"], ham,
+                                  ve.ve_default_options(precision=pcode, stream=stream.cuda_stream))
+                try:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    code, st = ve.ve_iterate(hh, args.ttb_max_iter, 1e-6)
+                    cert = ve.ve_bound(hh)
+                    el = time.perf_counter() - t0
+                    ttb[pname] = {"seconds": el, "sweeps": st.iter, "converged": code == 0,
+                                  "residual": st.residual, "bound_per_spin": cert.bound_per_spin,
+                                  "primal_per_spin": cert.primal_per_spin,
+                                  "iter_per_s": st.iter / el}
+                finally:
+                    ve.ve_destroy(hh)
+
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded spin Hamiltonian, no dataset)",
+            "config": workload_config(args, N, D),
+            "e2e": e2e, "gpu_launches": launches * world, "roofline": roof, "stages": stages,
+            "clocks": ck, "time_to_bound": ttb,
+            "last_status": {"iter": status.iter, "energy_per_spin": status.energy_per_spin,
+                            "feas_err": status.feas_err},
+        }
+    finally:
+        ve.ve_destroy(h)
+    if rank == 0 and world == 1:
+        rate, n, el, cores = oracle_rate(args.workload, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{n} full sweeps of {args.workload} in {el:.1f} s "
+                                         "(numpy float64 oracle, one warm-up sweep)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * ve.h -- C ABI of the GB300 solver for the variational-embedding semidefinite relaxation of
+ * Khoo & Lindsey, "Scalable semidefinite programming approach to variational embedding for
+ * quantum many-body problems" (arXiv:2106.02682).
+ *
+ * The solver runs the translation-invariant ADMM / projected dual-gradient ascent of the
+ * paper's Algorithm 6 (Sec. 3.3) on one GPU and returns a certified lower bound on the
+ * ground-state energy of a periodic spin-1/2 lattice.  One sweep is:
+ *   effective Hamiltonians from X (Eq. (effHam)); closed-form pair update (Eq. (rhoijUpdate));
+ *   PSD projection of every pair marginal (Eq. (rhoijTildeUpdate)); one-cluster marginal
+ *   update (Eq. (rhoiUpdate)); dual updates (Algorithm 4); X' = X - eps G; block DFT of X's
+ *   first block row; PSD projection of every wavevector block; inverse DFT.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: VE_OK (0), VE_NOT_CONVERGED (1) or a negative VE_E* code.  No entry point
+ *     aborts or prints; ve_error_string() names a code.
+ *   - Pointers documented "host" are read or written during the call only; the caller keeps
+ *     ownership.  Pointers documented "device" must be CUDA device (or managed) memory on the
+ *     current device, valid until the work issued on the given stream has completed.
+ *   - Matrices are row-major, float64.  Complex matrices are interleaved (re, im) float64.
+ *   - Cluster marginals are m x m (m = 2^L, L spins per cluster); pair marginals and X blocks
+ *     are D x D, D = m^2, with the pair basis index a*m + b (cluster 0 = first tensor factor).
+ *   - Cluster offsets delta are numbered row-major over the cluster lattice; pair arrays hold
+ *     delta = 1 .. N-1 (N = number of clusters), X holds delta = 0 .. N-1.
+ *   - Energies are per spin.
+ *   - A handle is used by one host thread at a time (thread-compatible, not thread-safe).
+ */
+#ifndef VE_H
+#define VE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VE_OK 0
+#define VE_NOT_CONVERGED 1
+#define VE_EINVAL (-1)       /* bad argument, shape or size                               */
+#define VE_ENOMEM (-2)       /* device or host allocation failed                          */
+#define VE_ECUDA (-3)        /* a CUDA call failed                                        */
+#define VE_ENONFINITE (-4)   /* the iteration produced a NaN or Inf                       */
+#define VE_EUNSUPPORTED (-5) /* valid but not implemented here (e.g. cluster size)        */
+
+#define VE_PREC_FP64 0  /* every step in float64                                          */
+#define VE_PREC_MIXED 1 /* PSD projections (eigensolve + reconstruction) in float32,
+                           everything else in float64; ve_iterate finishes in float64     */
+
+#define VE_MAX_BONDS 4
+
+/* Periodic lattice: dim = 1 or 2, extent[p] spins along axis p (extent[1] ignored if dim 1). */
+typedef struct {
+  int dim;
+  int extent[2];
+} ve_lattice;
+
+/* Rectangular cluster of extent[0] x extent[1] spins (Sec. 2.3); must tile the lattice. */
+typedef struct {
+  int extent[2];
+} ve_cluster;
+
+/* Translation-invariant real spin-1/2 Hamiltonian (Sec. 2.1):
+ *   H = sum_s onsite(s) + sum_s sum_b bond_b(s, s + bond_offset[b]).
+ * onsite: 2x2 real symmetric; bond[b]: 4x4 real symmetric acting on (s, s + offset) with s the
+ * first tensor factor; the spin basis is (sigma^z = +1, sigma^z = -1). */
+typedef struct {
+  double onsite[4];
+  int nbond;
+  int bond_offset[VE_MAX_BONDS][2];
+  double bond[VE_MAX_BONDS][16];
+} ve_hamiltonian;
+
+/* Algorithm parameters.  Defaults (ve_default_options) are those of Sec. 4: mu = nu = 10,
+ * eps = 2, VE_PREC_FP64, check_every = 10, stream = NULL (the handle creates its own). */
+typedef struct {
+  double mu, nu, eps;
+  int precision;   /* VE_PREC_FP64 or VE_PREC_MIXED */
+  int check_every; /* sweeps between residual read-backs in ve_iterate, >= 1 */
+  void* stream;    /* cudaStream_t for all of the handle's work, or NULL */
+} ve_options;
+
+/* Convergence measures after the last sweep (Sec. 4): energy per spin of the closed-form pair
+ * marginals with the bare Hamiltonian, feasibility error Eq. (feasErr), |energy change| between
+ * the last two sweeps, residual = max(feas_err, d_energy). */
+typedef struct {
+  long iter;
+  double energy_per_spin, feas_err, d_energy, residual;
+} ve_status;
+
+/* Certified lower bound (weak duality of Eq. (partialDual) with the Lagrangian of Eq.
+ * (lagrangian)): raw_bound (whole lattice) = N lmin(K_0) + sum_delta c(delta) lmin(K_delta);
+ * x_min_eig = smallest eigenvalue of the block-circulant X; x_neg_correction = N m max(0,
+ * -x_min_eig); bound_per_spin = (raw_bound - x_neg_correction) / spins.  primal_per_spin is
+ * the energy of the last sweep. */
+typedef struct {
+  double bound_per_spin, raw_bound, x_min_eig, x_neg_correction, primal_per_spin;
+} ve_cert;
+
+typedef struct ve_handle ve_handle;
+
+/* Fill *opt with the defaults above. */
+void ve_default_options(ve_options* opt);
+
+/* Transverse-field Ising site terms, Eq. (TFI): onsite -h sigma^x, bond -J sigma^z sigma^z along
+ * each lattice axis.  Returns VE_EINVAL for dim not 1 or 2 or out == NULL. */
+int ve_ham_tfim(int dim, double J, double h, ve_hamiltonian* out);
+
+/* XXZ site terms J (sigma^x sigma^x + sigma^y sigma^y + delta sigma^z sigma^z) along each axis;
+ * delta = 1 is the antiferromagnetic Heisenberg model, Eq. (AFH). */
+int ve_ham_xxz(int dim, double J, double delta, ve_hamiltonian* out);
+
+/* Build the cluster blocks H_0, H_{0,delta} (Sec. 2.3, 3.3), allocate the device state and
+ * initialise it as in Sec. 4 (Lambda = 0, rho_0 = I/m, rho~ = I/D, X = I).
+ * Supported: L = spins per cluster in {1, 2, 3}; clusters per axis M_p >= 1 with N >= 2; 1-D
+ * lattices with N <= 4096 factoring as N1*N2, N1, N2 <= 64; 2-D lattices with M_p <= 64.
+ * opt may be NULL (defaults).  On success *out owns all device memory until ve_destroy.
+ * Errors: VE_EINVAL (bad shape, cluster does not tile the lattice, N < 2, bad options),
+ * VE_EUNSUPPORTED (sizes outside the list above), VE_ENOMEM, VE_ECUDA. */
+int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_hamiltonian* ham,
+              const ve_options* opt, ve_handle** out);
+
+/* Run sweeps of Algorithm 6 until max_iter sweeps or, when tol > 0, until the residual is
+ * <= tol at a read-back (every check_every sweeps).  In VE_PREC_MIXED the sweeps use float32
+ * projections until the residual reaches 10 * tol (or stalls), then continue in float64.
+ * Writes the last status to *out (may be NULL).  Returns VE_OK if converged (or tol <= 0 and
+ * max_iter sweeps ran), VE_NOT_CONVERGED, VE_ENONFINITE, VE_EINVAL, VE_ECUDA.  Synchronous. */
+int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out);
+
+/* Certified lower bound of the current state, all in float64 on the GPU (eigenvalues by
+ * Jacobi).  Synchronous.  Errors: VE_EINVAL, VE_ECUDA. */
+int ve_bound(ve_handle* h, ve_cert* out);
+
+/* Release everything the handle owns.  NULL-safe. */
+void ve_destroy(ve_handle* h);
+
+/* Sizes of the instance: clusters N, cluster dimension m, pair dimension D (any may be NULL). */
+int ve_dims(const ve_handle* h, int* N, int* m, int* D);
+
+/* Packed state: rho_0 (m^2), rho~ (P D^2), Lambda (P D^2), Lambda1 (P m^2), Lambda2 (P m^2),
+ * X (N D^2), P = N - 1, float64, each block row-major.  ve_state_size gives the byte count;
+ * get/set copy through `host` (host memory, bytes must equal that size; VE_EINVAL otherwise).
+ * ve_set_state clears the stored previous energy, so the next d_energy is +inf. */
+size_t ve_state_size(const ve_handle* h);
+int ve_get_state(ve_handle* h, double* host, size_t bytes);
+int ve_set_state(ve_handle* h, const double* host, size_t bytes);
+
+/* Last status of the handle without running a sweep. */
+int ve_get_status(ve_handle* h, ve_status* out);
+
+/* Per-stage timing.  ve_profile(h, 1) clears the accumulators and makes every following sweep
+ * run uncaptured with CUDA events (on the handle's stream) around each of its VE_NSTAGE stages:
+ * 0 pair pass, 1 rho_0 update, 2 Lambda1/Lambda2 update, 3 status, 4 forward block DFT,
+ * 5 per-wavevector projection, 6 inverse block DFT.  ve_profile(h, 0) returns to graph replay.
+ * ve_profile_read writes accumulated milliseconds and kernel launches per stage (arrays of
+ * VE_NSTAGE, host).  Errors: VE_EINVAL, VE_ECUDA. */
+#define VE_NSTAGE 7
+int ve_profile(ve_handle* h, int enable);
+int ve_profile_read(ve_handle* h, double* ms, long* launches);
+
+/* Name of a status code (static string). */
+const char* ve_error_string(int code);
+
+/* ---- batched building blocks on caller device memory ------------------------------------ */
+
+/* Pi_{>=0} (Sec. 3, the Frobenius-nearest PSD matrix, Eq. (rhoijTildeUpdate)) of `count` real
+ * symmetric n x n matrices: in, out = device pointers to count*n*n float64 (in == out allowed).
+ * n in {2, 4, 8, 16, 64}; precision VE_PREC_FP64 or VE_PREC_MIXED (float32 eigensolve).  The
+ * input is symmetrised as (A + A^T)/2.  Asynchronous on `stream` (cudaStream_t or NULL).
+ * Errors: VE_EINVAL (n, count < 0, precision), VE_ECUDA (launch failure). */
+int ve_project_psd_sym(const double* in, double* out, int n, long count, int precision,
+                       void* stream);
+
+/* Same for complex Hermitian n x n matrices (Algorithm 6, the per-wavevector projection),
+ * interleaved complex: count*n*n*2 float64 each; n in {4, 16, 64}. */
+int ve_project_psd_herm(const double* in, double* out, int n, long count, int precision,
+                        void* stream);
+
+/* The global X step of Algorithm 6 on a first block row, without the G term: given X'_{0,delta}
+ * (N blocks D x D, device, N = M0*M1 clusters of a dim-1 or dim-2 cluster lattice with M[p]
+ * clusters per axis), write X_{0,delta} = (1/N) sum_k e^{+i 2 pi delta.k/M} Pi_{>=0}(C_k),
+ * C_k = sum_delta e^{-i 2 pi delta.k/M} X'_{0,delta}.  The input must satisfy
+ * X'_{0,-delta} = X'_{0,delta}^T (then every C_k is Hermitian); it may alias the output.
+ * workspace: device buffer of at least ve_circulant_workspace_size(...) bytes, 256-byte
+ * aligned.  D in {4, 16, 64}.  Asynchronous on `stream`.  Errors: VE_EINVAL (sizes, NULL,
+ * small workspace), VE_EUNSUPPORTED (lattice not factorable as for ve_create), VE_ECUDA. */
+size_t ve_circulant_workspace_size(int dim, const int M[2], int D);
+int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M[2], int D,
+                         int precision, void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VE_H */

@@ -1,0 +1,746 @@
+// ve_api.cu -- host side of the C ABI declared in include/ve.h: cluster-model construction,
+// device state, sweep orchestration (CUDA graphs), certified bound assembly, and the
+// standalone batched entry points.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <vector>
+
+#include "../../include/ve.h"
+#include "ve_internal.h"
+
+using namespace ve;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Embed a one-site operator h (2x2) on spin i / a two-site operator B (4x4) on spins (i, j) --
+// B's first factor on spin i -- into the 2^K-dimensional space of K spins (spin 0 = first
+// Kronecker factor).  Accumulates into out (row-major 2^K x 2^K).
+void embed1(const double* h, int i, int K, double* out) {
+  const int dim = 1 << K, sh = K - 1 - i;
+  for (int col = 0; col < dim; ++col) {
+    const int sc = (col >> sh) & 1;
+    for (int sr = 0; sr < 2; ++sr) {
+      const double amp = h[sr * 2 + sc];
+      if (amp == 0.0) continue;
+      const int row = (col & ~(1 << sh)) | (sr << sh);
+      out[(size_t)row * dim + col] += amp;
+    }
+  }
+}
+
+void embed2(const double* B, int i, int j, int K, double* out) {
+  const int dim = 1 << K, si = K - 1 - i, sj = K - 1 - j;
+  for (int col = 0; col < dim; ++col) {
+    const int sc = (((col >> si) & 1) << 1) | ((col >> sj) & 1);
+    for (int sr = 0; sr < 4; ++sr) {
+      const double amp = B[sr * 4 + sc];
+      if (amp == 0.0) continue;
+      int row = col & ~(1 << si) & ~(1 << sj);
+      row |= ((sr >> 1) & 1) << si;
+      row |= (sr & 1) << sj;
+      out[(size_t)row * dim + col] += amp;
+    }
+  }
+}
+
+struct Model {
+  int dim, e0, e1, c0, c1, M0, M1, N, L, m, D;
+  std::vector<double> H0;                       // m*m
+  std::map<int, std::vector<double>> pair;      // linear delta -> D*D
+  std::vector<int> neg;                         // N
+  std::vector<long long> count;                 // N, c(delta)
+};
+
+// Cluster blocks of a translation-invariant lattice (Sec. 2.3 / 3.3 of the paper): every term
+// starting on a spin of cluster 0 is placed in H_0 (both ends in cluster 0) or in the pair
+// block of the cluster it reaches, and its translate -- the same term seen from the other
+// cluster -- in the pair block of the opposite offset with the factors swapped.
+int build_model(const ve_lattice* lat, const ve_cluster* clu, const ve_hamiltonian* ham, Model& md) {
+  if (!lat || !clu || !ham) return VE_EINVAL;
+  md.dim = lat->dim;
+  if (md.dim != 1 && md.dim != 2) return VE_EINVAL;
+  md.e0 = lat->extent[0];
+  md.e1 = md.dim == 2 ? lat->extent[1] : 1;
+  md.c0 = clu->extent[0];
+  md.c1 = md.dim == 2 ? clu->extent[1] : 1;
+  if (md.e0 < 1 || md.e1 < 1 || md.c0 < 1 || md.c1 < 1) return VE_EINVAL;
+  if (md.e0 % md.c0 || md.e1 % md.c1) return VE_EINVAL;
+  md.M0 = md.e0 / md.c0;
+  md.M1 = md.e1 / md.c1;
+  md.N = md.M0 * md.M1;
+  md.L = md.c0 * md.c1;
+  if (md.N < 2) return VE_EINVAL;
+  if (md.L < 1 || md.L > 3) return VE_EUNSUPPORTED;
+  if (ham->nbond < 0 || ham->nbond > VE_MAX_BONDS) return VE_EINVAL;
+  md.m = 1 << md.L;
+  md.D = md.m * md.m;
+  const int L = md.L, D = md.D;
+  md.H0.assign((size_t)md.m * md.m, 0.0);
+  md.pair.clear();
+  auto lin = [&](int X, int Y) { return X * md.M1 + Y; };
+  auto negl = [&](int dl) {
+    const int X = dl / md.M1, Y = dl % md.M1;
+    return lin((md.M0 - X) % md.M0, (md.M1 - Y) % md.M1);
+  };
+  for (int x = 0; x < md.c0; ++x) {
+    for (int y = 0; y < md.c1; ++y) {
+      const int u = x * md.c1 + y;
+      embed1(ham->onsite, u, L, md.H0.data());
+      for (int b = 0; b < ham->nbond; ++b) {
+        const int ox = ham->bond_offset[b][0], oy = md.dim == 2 ? ham->bond_offset[b][1] : 0;
+        const int tx = ((x + ox) % md.e0 + md.e0) % md.e0;
+        const int ty = ((y + oy) % md.e1 + md.e1) % md.e1;
+        const int tX = tx / md.c0, tY = ty / md.c1;
+        const int ut = (tx % md.c0) * md.c1 + (ty % md.c1);
+        const double* B = ham->bond[b];
+        if (tX == 0 && tY == 0) {
+          if (ut == u) return VE_EINVAL;  // a bond from a spin to itself
+          embed2(B, u, ut, L, md.H0.data());
+        } else {
+          const int dl = lin(tX, tY), nd = negl(dl);
+          auto& blk = md.pair[dl];
+          if (blk.empty()) blk.assign((size_t)D * D, 0.0);
+          embed2(B, u, L + ut, 2 * L, blk.data());
+          auto& nblk = md.pair[nd];
+          if (nblk.empty()) nblk.assign((size_t)D * D, 0.0);
+          embed2(B, L + u, ut, 2 * L, nblk.data());
+        }
+      }
+    }
+  }
+  md.neg.resize(md.N);
+  for (int dl = 0; dl < md.N; ++dl) md.neg[dl] = negl(dl);
+  // c(delta) = #{a : l(a) < l(a + delta)}, l = row-major linear index
+  md.count.assign(md.N, 0);
+  for (int dl = 1; dl < md.N; ++dl) {
+    const int dX = dl / md.M1, dY = dl % md.M1;
+    long long c = 0;
+    for (int a = 0; a < md.N; ++a) {
+      const int aX = a / md.M1, aY = a % md.M1;
+      if (lin((aX + dX) % md.M0, (aY + dY) % md.M1) > a) ++c;
+    }
+    md.count[dl] = c;
+  }
+  return VE_OK;
+}
+
+}  // namespace
+
+struct ve_handle {
+  Model md;
+  ve_options opt;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  FftPlan plan;
+  int P = 0;
+  // device memory
+  void* dev = nullptr;  // one allocation, carved below
+  size_t state_bytes = 0;
+  double *state = nullptr, *rho0 = nullptr, *rt = nullptr, *lam = nullptr, *lam1 = nullptr,
+         *lam2 = nullptr, *X = nullptr;
+  double *a1r = nullptr, *a2r = nullptr, *part = nullptr, *part2 = nullptr, *hb = nullptr,
+         *H0 = nullptr, *lmin_pairs = nullptr, *lmin_k = nullptr, *lmin0 = nullptr;
+  int *hslot = nullptr, *neg = nullptr;
+  double2 *specA = nullptr, *specB = nullptr, *tw = nullptr;
+  DevStatus* dst = nullptr;
+  DevStatus* hst = nullptr;  // pinned
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  bool warmed[2] = {false, false};
+  bool fp64_phase = false;  // MIXED: switched to float64
+  // per-stage profiling
+  bool prof = false;
+  cudaEvent_t ev[VE_NSTAGE + 1] = {};
+  double prof_ms[VE_NSTAGE] = {};
+  long prof_launch[VE_NSTAGE] = {};
+  int stage_launches[VE_NSTAGE] = {};
+};
+
+namespace {
+
+#define VE_CU(call)                       \
+  do {                                    \
+    cudaError_t _e = (call);              \
+    if (_e != cudaSuccess) return VE_ECUDA; \
+  } while (0)
+
+PairArgs pair_args(ve_handle* h) {
+  PairArgs a;
+  a.N = h->md.N;
+  a.P = h->P;
+  a.m = h->md.m;
+  a.D = h->md.D;
+  a.mu = h->opt.mu;
+  a.nu = h->opt.nu;
+  a.eps = h->opt.eps;
+  a.rho0 = h->rho0;
+  a.rt = h->rt;
+  a.lam = h->lam;
+  a.lam1 = h->lam1;
+  a.lam2 = h->lam2;
+  a.X = h->X;
+  a.hb = h->hb;
+  a.hslot = h->hslot;
+  a.a1r = h->a1r;
+  a.a2r = h->a2r;
+  a.part = h->part;
+  return a;
+}
+
+SmallArgs small_args(ve_handle* h) {
+  SmallArgs a;
+  a.N = h->md.N;
+  a.P = h->P;
+  a.m = h->md.m;
+  a.D = h->md.D;
+  a.L = h->md.L;
+  a.mu = h->opt.mu;
+  a.nu = h->opt.nu;
+  a.eps = h->opt.eps;
+  a.rho0 = h->rho0;
+  a.lam1 = h->lam1;
+  a.lam2 = h->lam2;
+  a.X = h->X;
+  a.H0 = h->H0;
+  a.a1r = h->a1r;
+  a.a2r = h->a2r;
+  a.part = h->part;
+  a.part2 = h->part2;
+  a.st = h->dst;
+  return a;
+}
+
+// One sweep of Algorithm 6, all on h->stream (with stage events when profiling).
+cudaError_t issue_sweep(ve_handle* h, bool fp32) {
+  cudaStream_t s = h->stream;
+  const PairArgs pa = pair_args(h);
+  const SmallArgs sa = small_args(h);
+  cudaError_t e;
+  auto mark = [&](int i) { return h->prof ? cudaEventRecord(h->ev[i], s) : cudaSuccess; };
+  if ((e = mark(0)) != cudaSuccess) return e;
+  if ((e = launch_pair(pa, fp32, s)) != cudaSuccess) return e;
+  if ((e = mark(1)) != cudaSuccess) return e;
+  if ((e = launch_rho0(sa, s)) != cudaSuccess) return e;
+  if ((e = mark(2)) != cudaSuccess) return e;
+  if ((e = launch_dual12(sa, s)) != cudaSuccess) return e;
+  if ((e = mark(3)) != cudaSuccess) return e;
+  if ((e = launch_status(sa, s)) != cudaSuccess) return e;
+  if ((e = mark(4)) != cudaSuccess) return e;
+  double2* spec = nullptr;
+  if ((e = fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, s)) != cudaSuccess) return e;
+  if ((e = mark(5)) != cudaSuccess) return e;
+  if ((e = launch_xproj(h->plan, spec, fp32, s)) != cudaSuccess) return e;
+  if ((e = mark(6)) != cudaSuccess) return e;
+  if ((e = fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, s)) != cudaSuccess) return e;
+  return mark(7);
+}
+
+// Add the stage times of the last profiled sweep (its events have completed).
+int accumulate_profile(ve_handle* h) {
+  for (int i = 0; i < VE_NSTAGE; ++i) {
+    float ms = 0.f;
+    VE_CU(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
+    h->prof_ms[i] += ms;
+    h->prof_launch[i] += h->stage_launches[i];
+  }
+  return VE_OK;
+}
+
+// Run `count` sweeps: the first one of each precision directly (kernel attributes are set
+// outside any capture), the rest by replaying a captured one-sweep graph.
+int read_status(ve_handle* h, ve_status* out);
+
+int run_sweeps(ve_handle* h, long count, bool fp32) {
+  const int v = fp32 ? 1 : 0;
+  if (count <= 0) return VE_OK;
+  if (h->prof) {
+    for (long i = 0; i < count; ++i) {
+      VE_CU(issue_sweep(h, fp32));
+      VE_CU(cudaStreamSynchronize(h->stream));
+      const int r = accumulate_profile(h);
+      if (r != VE_OK) return r;
+    }
+    h->warmed[v] = true;
+    return VE_OK;
+  }
+  if (!h->warmed[v]) {
+    VE_CU(issue_sweep(h, fp32));
+    h->warmed[v] = true;
+    --count;
+  }
+  if (count <= 0) return VE_OK;
+  if (!h->exec[v]) {
+    VE_CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = issue_sweep(h, fp32);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return VE_ECUDA;
+    }
+    h->graph[v] = g;
+    VE_CU(cudaGraphInstantiate(&h->exec[v], g, 0));
+  }
+  for (long i = 0; i < count; ++i) VE_CU(cudaGraphLaunch(h->exec[v], h->stream));
+  return VE_OK;
+}
+
+int read_status(ve_handle* h, ve_status* out) {
+  VE_CU(cudaMemcpyAsync(h->hst, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+  VE_CU(cudaStreamSynchronize(h->stream));
+  if (out) {
+    out->iter = (long)h->hst->iter;
+    out->energy_per_spin = h->hst->energy;
+    out->feas_err = h->hst->feas;
+    out->d_energy = h->hst->d_energy;
+    out->residual = h->hst->residual;
+  }
+  return VE_OK;
+}
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&old_);
+    if (old_ != dev) cudaSetDevice(dev);
+    dev_ = dev;
+  }
+  ~DeviceGuard() {
+    if (old_ != dev_) cudaSetDevice(old_);
+  }
+
+ private:
+  int old_ = 0, dev_ = 0;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* ve_error_string(int code) {
+  switch (code) {
+    case VE_OK: return "ok";
+    case VE_NOT_CONVERGED: return "not converged";
+    case VE_EINVAL: return "invalid argument";
+    case VE_ENOMEM: return "out of memory";
+    case VE_ECUDA: return "CUDA error";
+    case VE_ENONFINITE: return "non-finite value in the iteration";
+    case VE_EUNSUPPORTED: return "unsupported size";
+    default: return "unknown status";
+  }
+}
+
+void ve_default_options(ve_options* opt) {
+  if (!opt) return;
+  opt->mu = 10.0;
+  opt->nu = 10.0;
+  opt->eps = 2.0;
+  opt->precision = VE_PREC_FP64;
+  opt->check_every = 10;
+  opt->stream = nullptr;
+}
+
+int ve_ham_tfim(int dim, double J, double h, ve_hamiltonian* out) {
+  if (!out || (dim != 1 && dim != 2)) return VE_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->onsite[1] = -h;
+  out->onsite[2] = -h;
+  out->nbond = dim;
+  for (int b = 0; b < dim; ++b) {
+    out->bond_offset[b][0] = (b == 0);
+    out->bond_offset[b][1] = (b == 1);
+    out->bond[b][0] = -J;
+    out->bond[b][5] = J;
+    out->bond[b][10] = J;
+    out->bond[b][15] = -J;
+  }
+  return VE_OK;
+}
+
+int ve_ham_xxz(int dim, double J, double delta, ve_hamiltonian* out) {
+  if (!out || (dim != 1 && dim != 2)) return VE_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->nbond = dim;
+  for (int b = 0; b < dim; ++b) {
+    out->bond_offset[b][0] = (b == 0);
+    out->bond_offset[b][1] = (b == 1);
+    // s^x s^x + s^y s^y = 2 (|01><10| + |10><01|); s^z s^z = diag(1, -1, -1, 1)
+    out->bond[b][0] = J * delta;
+    out->bond[b][5] = -J * delta;
+    out->bond[b][10] = -J * delta;
+    out->bond[b][15] = J * delta;
+    out->bond[b][6] = 2.0 * J;
+    out->bond[b][9] = 2.0 * J;
+  }
+  return VE_OK;
+}
+
+int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_hamiltonian* ham,
+              const ve_options* opt, ve_handle** out) {
+  if (!out) return VE_EINVAL;
+  *out = nullptr;
+  ve_handle* h = new (std::nothrow) ve_handle();
+  if (!h) return VE_ENOMEM;
+  int rc = build_model(lattice, cluster, ham, h->md);
+  if (rc != VE_OK) {
+    delete h;
+    return rc;
+  }
+  if (opt) {
+    h->opt = *opt;
+  } else {
+    ve_default_options(&h->opt);
+  }
+  if (!(h->opt.mu > 0) || !(h->opt.nu > 0) || !(h->opt.eps > 0) || h->opt.check_every < 1 ||
+      (h->opt.precision != VE_PREC_FP64 && h->opt.precision != VE_PREC_MIXED)) {
+    delete h;
+    return VE_EINVAL;
+  }
+  const int Ms[2] = {h->md.M0, h->md.M1};
+  rc = fft_plan_build(h->plan, h->md.dim, Ms, h->md.D);
+  if (rc != 0) {
+    delete h;
+    return rc;
+  }
+  cudaGetDevice(&h->device);
+  const Model& md = h->md;
+  const int N = md.N, m = md.m, D = md.D, P = N - 1;
+  h->P = P;
+  const size_t mm = (size_t)m * m, DD = (size_t)D * D;
+  h->state_bytes = sizeof(double) * (mm + 2 * P * DD + 2 * P * mm + N * DD);
+  const int nb = (int)md.pair.size();
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t o_state = take(h->state_bytes);
+  const size_t o_a1r = take(sizeof(double) * P * mm);
+  const size_t o_a2r = take(sizeof(double) * P * mm);
+  const size_t o_part = take(sizeof(double) * 2 * P);
+  const size_t o_part2 = take(sizeof(double) * P);
+  const size_t o_hb = take(sizeof(double) * (nb > 0 ? nb : 1) * DD);
+  const size_t o_H0 = take(sizeof(double) * mm);
+  const size_t o_lp = take(sizeof(double) * P);
+  const size_t o_lk = take(sizeof(double) * N);
+  const size_t o_l0 = take(sizeof(double));
+  const size_t o_hslot = take(sizeof(int) * N);
+  const size_t o_neg = take(sizeof(int) * N);
+  const size_t o_sa = take(sizeof(double2) * N * h->plan.E);
+  const size_t o_sb = take(sizeof(double2) * N * h->plan.E);
+  const size_t o_tw = take(sizeof(double2) * h->plan.ntw);
+  const size_t o_st = take(sizeof(DevStatus));
+  if (cudaMalloc(&h->dev, off) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return VE_ENOMEM;
+  }
+  if (cudaMallocHost((void**)&h->hst, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->dev);
+    delete h;
+    return VE_ENOMEM;
+  }
+  char* base = (char*)h->dev;
+  h->state = (double*)(base + o_state);
+  h->rho0 = h->state;
+  h->rt = h->rho0 + mm;
+  h->lam = h->rt + P * DD;
+  h->lam1 = h->lam + P * DD;
+  h->lam2 = h->lam1 + P * mm;
+  h->X = h->lam2 + P * mm;
+  h->a1r = (double*)(base + o_a1r);
+  h->a2r = (double*)(base + o_a2r);
+  h->part = (double*)(base + o_part);
+  h->part2 = (double*)(base + o_part2);
+  h->hb = (double*)(base + o_hb);
+  h->H0 = (double*)(base + o_H0);
+  h->lmin_pairs = (double*)(base + o_lp);
+  h->lmin_k = (double*)(base + o_lk);
+  h->lmin0 = (double*)(base + o_l0);
+  h->hslot = (int*)(base + o_hslot);
+  h->neg = (int*)(base + o_neg);
+  h->specA = (double2*)(base + o_sa);
+  h->specB = (double2*)(base + o_sb);
+  h->tw = (double2*)(base + o_tw);
+  h->dst = (DevStatus*)(base + o_st);
+  if (h->opt.stream) {
+    h->stream = (cudaStream_t)h->opt.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      ve_destroy(h);
+      return VE_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  // host staging: initial state (Sec. 4), Hamiltonian blocks, index tables
+  std::vector<double> st(h->state_bytes / sizeof(double), 0.0);
+  for (int i = 0; i < m; ++i) st[(size_t)i * m + i] = 1.0 / m;
+  for (int p = 0; p < P; ++p)
+    for (int i = 0; i < D; ++i) st[mm + (size_t)p * DD + (size_t)i * D + i] = 1.0 / D;
+  const size_t xo = mm + 2 * P * DD + 2 * P * mm;
+  for (int i = 0; i < D; ++i) st[xo + (size_t)i * D + i] = 1.0;
+  std::vector<double> hb((size_t)(nb > 0 ? nb : 1) * DD, 0.0);
+  std::vector<int> hslot(N, -1);
+  int k = 0;
+  for (auto& kv : md.pair) {
+    hslot[kv.first] = k;
+    memcpy(hb.data() + (size_t)k * DD, kv.second.data(), sizeof(double) * DD);
+    ++k;
+  }
+  DevStatus ds;
+  memset(&ds, 0, sizeof(ds));
+  ds.e_prev = NAN;
+  ds.energy = NAN;
+  ds.feas = NAN;
+  ds.d_energy = INFINITY;
+  ds.residual = INFINITY;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->state, st.data(), h->state_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->hb, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->H0, md.H0.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->hslot, hslot.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->neg, md.neg.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->dst, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_fft_tables(h->plan, h->tw, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    ve_destroy(h);
+    return VE_ECUDA;
+  }
+  *h->hst = ds;
+  const int launches[VE_NSTAGE] = {1, 1, 1, 1, h->plan.npass, 1, h->plan.npass};
+  for (int i = 0; i < VE_NSTAGE; ++i) h->stage_launches[i] = launches[i];
+  *out = h;
+  return VE_OK;
+}
+
+void ve_destroy(ve_handle* h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int v = 0; v < 2; ++v) {
+    if (h->exec[v]) cudaGraphExecDestroy(h->exec[v]);
+    if (h->graph[v]) cudaGraphDestroy(h->graph[v]);
+  }
+  for (int i = 0; i <= VE_NSTAGE; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->hst) cudaFreeHost(h->hst);
+  if (h->dev) cudaFree(h->dev);
+  delete h;
+}
+
+int ve_dims(const ve_handle* h, int* N, int* m, int* D) {
+  if (!h) return VE_EINVAL;
+  if (N) *N = h->md.N;
+  if (m) *m = h->md.m;
+  if (D) *D = h->md.D;
+  return VE_OK;
+}
+
+size_t ve_state_size(const ve_handle* h) { return h ? h->state_bytes : 0; }
+
+int ve_get_state(ve_handle* h, double* host, size_t bytes) {
+  if (!h || !host || bytes != h->state_bytes) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  VE_CU(cudaMemcpyAsync(host, h->state, bytes, cudaMemcpyDeviceToHost, h->stream));
+  VE_CU(cudaStreamSynchronize(h->stream));
+  return VE_OK;
+}
+
+int ve_set_state(ve_handle* h, const double* host, size_t bytes) {
+  if (!h || !host || bytes != h->state_bytes) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  VE_CU(cudaStreamSynchronize(h->stream));
+  const int r = read_status(h, nullptr);
+  if (r != VE_OK) return r;
+  h->hst->e_prev = NAN;
+  h->hst->d_energy = INFINITY;
+  h->hst->residual = INFINITY;
+  VE_CU(cudaMemcpyAsync(h->state, host, bytes, cudaMemcpyHostToDevice, h->stream));
+  VE_CU(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
+  VE_CU(cudaStreamSynchronize(h->stream));
+  h->fp64_phase = false;
+  return VE_OK;
+}
+
+int ve_profile(ve_handle* h, int enable) {
+  if (!h) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  if (enable) {
+    for (int i = 0; i <= VE_NSTAGE; ++i)
+      if (!h->ev[i]) VE_CU(cudaEventCreate(&h->ev[i]));
+    for (int i = 0; i < VE_NSTAGE; ++i) {
+      h->prof_ms[i] = 0.0;
+      h->prof_launch[i] = 0;
+    }
+  }
+  h->prof = enable != 0;
+  return VE_OK;
+}
+
+int ve_profile_read(ve_handle* h, double* ms, long* launches) {
+  if (!h || !ms || !launches) return VE_EINVAL;
+  for (int i = 0; i < VE_NSTAGE; ++i) {
+    ms[i] = h->prof_ms[i];
+    launches[i] = h->prof_launch[i];
+  }
+  return VE_OK;
+}
+
+int ve_get_status(ve_handle* h, ve_status* out) {
+  if (!h || !out) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  return read_status(h, out);
+}
+
+int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out) {
+  if (!h || max_iter < 0) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  const bool mixed = h->opt.precision == VE_PREC_MIXED;
+  ve_status s;
+  int rc = VE_NOT_CONVERGED;
+  long done = 0;
+  double best = INFINITY;
+  int stall = 0;
+  if (max_iter == 0) {
+    int r = read_status(h, &s);
+    if (out) *out = s;
+    return r != VE_OK ? r : VE_OK;
+  }
+  while (done < max_iter) {
+    const long chunk = (long)h->opt.check_every < max_iter - done ? (long)h->opt.check_every : max_iter - done;
+    const bool fp32 = mixed && !h->fp64_phase;
+    int r = run_sweeps(h, chunk, fp32);
+    if (r != VE_OK) return r;
+    r = read_status(h, &s);
+    if (r != VE_OK) return r;
+    done += chunk;
+    if (!isfinite(s.energy_per_spin) || !isfinite(s.feas_err)) {
+      if (out) *out = s;
+      return VE_ENONFINITE;
+    }
+    if (tol > 0) {
+      if (fp32) {
+        // float32 projections until the residual is within 10x of the target or stops falling
+        if (s.residual < 0.99 * best) {
+          best = s.residual;
+          stall = 0;
+        } else {
+          ++stall;
+        }
+        if (s.residual <= 10.0 * tol || stall >= 20) h->fp64_phase = true;
+      } else if (s.residual <= tol) {
+        rc = VE_OK;
+        break;
+      }
+    }
+  }
+  if (tol <= 0) rc = VE_OK;
+  if (out) *out = s;
+  return rc;
+}
+
+int ve_bound(ve_handle* h, ve_cert* out) {
+  if (!h || !out) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  const Model& md = h->md;
+  const int N = md.N, P = h->P;
+  double2* spec = nullptr;
+  VE_CU(fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, h->stream));
+  VE_CU(launch_xeig(h->plan, spec, h->lmin_k, h->stream));
+  BoundArgs b;
+  b.N = N;
+  b.P = P;
+  b.m = md.m;
+  b.D = md.D;
+  b.X = h->X;
+  b.lam1 = h->lam1;
+  b.hb = h->hb;
+  b.hslot = h->hslot;
+  b.neg = h->neg;
+  b.H0 = h->H0;
+  b.lmin_pairs = h->lmin_pairs;
+  b.lmin0 = h->lmin0;
+  VE_CU(launch_bound(b, h->stream));
+  std::vector<double> lp(P), lk(N);
+  double l0 = 0;
+  VE_CU(cudaMemcpyAsync(lp.data(), h->lmin_pairs, sizeof(double) * P, cudaMemcpyDeviceToHost, h->stream));
+  VE_CU(cudaMemcpyAsync(lk.data(), h->lmin_k, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  VE_CU(cudaMemcpyAsync(&l0, h->lmin0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  ve_status s;
+  int r = read_status(h, &s);  // synchronises the stream
+  if (r != VE_OK) return r;
+  double raw = (double)N * l0;
+  for (int p = 0; p < P; ++p) raw += (double)md.count[p + 1] * lp[p];
+  double xmin = INFINITY;
+  for (int k = 0; k < N; ++k) xmin = lk[k] < xmin ? lk[k] : xmin;
+  const double corr = (double)N * md.m * (xmin < 0 ? -xmin : 0.0);
+  const double spins = (double)N * md.L;
+  out->raw_bound = raw;
+  out->x_min_eig = xmin;
+  out->x_neg_correction = corr;
+  out->bound_per_spin = (raw - corr) / spins;
+  out->primal_per_spin = s.energy_per_spin;
+  return VE_OK;
+}
+
+int ve_project_psd_sym(const double* in, double* out, int n, long count, int precision,
+                       void* stream) {
+  if (!in || !out || count < 0) return VE_EINVAL;
+  if (n != 2 && n != 4 && n != 8 && n != 16 && n != 64) return VE_EINVAL;
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
+  VE_CU(launch_proj_sym(in, out, n, count, precision == VE_PREC_MIXED, (cudaStream_t)stream));
+  return VE_OK;
+}
+
+int ve_project_psd_herm(const double* in, double* out, int n, long count, int precision,
+                        void* stream) {
+  if (!in || !out || count < 0) return VE_EINVAL;
+  if (n != 4 && n != 16 && n != 64) return VE_EINVAL;
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
+  VE_CU(launch_proj_herm(in, out, n, count, precision == VE_PREC_MIXED, (cudaStream_t)stream));
+  return VE_OK;
+}
+
+size_t ve_circulant_workspace_size(int dim, const int M[2], int D) {
+  if (!M) return 0;
+  FftPlan p;
+  if (fft_plan_build(p, dim, M, D) != 0) return 0;
+  return align_up(sizeof(double2) * (size_t)p.N * p.E) * 2 + align_up(sizeof(double2) * p.ntw);
+}
+
+int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M[2], int D,
+                         int precision, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!x_in || !x_out || !M || !workspace) return VE_EINVAL;
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
+  if (((uintptr_t)workspace) % kAlign) return VE_EINVAL;
+  FftPlan p;
+  const int rc = fft_plan_build(p, dim, M, D);
+  if (rc != 0) return rc;
+  const size_t sb = align_up(sizeof(double2) * (size_t)p.N * p.E);
+  if (workspace_bytes < 2 * sb + align_up(sizeof(double2) * p.ntw)) return VE_EINVAL;
+  char* w = (char*)workspace;
+  double2* A = (double2*)w;
+  double2* B = (double2*)(w + sb);
+  double2* tw = (double2*)(w + 2 * sb);
+  cudaStream_t s = (cudaStream_t)stream;
+  VE_CU(launch_fft_tables(p, tw, s));
+  double2* spec = nullptr;
+  VE_CU(fft_forward(p, x_in, A, B, tw, &spec, s));
+  VE_CU(launch_xproj(p, spec, precision == VE_PREC_MIXED, s));
+  VE_CU(fft_inverse(p, spec, A, B, x_out, tw, s));
+  return VE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,443 @@
+// ve_fft.cu -- the global X step of Algorithm 6 (Khoo & Lindsey, arXiv:2106.02682, Sec. 3.3):
+// block DFT of X's first block row over the cluster offsets, per-wavevector PSD projection of
+// the Hermitian blocks, inverse DFT.
+//
+// Layout.  The first block row is N slots (cluster offsets, row-major) of D*D reals.  Because
+// every entry sequence over delta is real, two entries share one complex sequence:
+// z_t[e] = X_t[e] + i X_t[e + E], E = D*D/2.  After the forward transform the true blocks are
+// recovered per wavevector from z[k] and conj(z[-k]); the inverse transform of
+// Y_k[e] + i Y_k[e + E] returns both real entry sequences at once.
+//
+// Transform.  Each pass is a length-n DFT (n <= 64) along one axis of the slot array viewed as
+// [A][n][B], done in shared memory by one CTA per (line, chunk of entries): radix-2 in place
+// when n is a power of two, the direct sum otherwise.  A 1-D lattice with N > 64 clusters uses
+// the four-step split N = N1 * N2 with a twiddle between the two passes; the spectrum is then
+// stored digit-reversed (slot c*N2 + e holds k = c + N1*e), which the projection handles through
+// the partner map k -> -k.  A 2-D lattice takes one pass per axis.  Forward sign e^{-i}, no
+// scaling; the projection kernel applies 1/N.
+#include <math.h>
+
+#include "../../include/ve.h"
+#include "ve_device.cuh"
+#include "ve_internal.h"
+
+namespace ve {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ int bitrev(int j, int logn) { return (int)(__brev((unsigned)j) >> (32 - logn)); }
+
+constexpr int FFT_EC = 32;        // entries per CTA
+constexpr int FFT_THREADS = 256;
+
+__global__ void __launch_bounds__(FFT_THREADS)
+    k_fft_pass(const double* __restrict__ xin, const double2* __restrict__ cin, double2* cout,
+               double* xout, const FftPass ps, const int dir, const int E,
+               const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) double2 sbuf[];
+  const int line = blockIdx.x;
+  const int la = line / ps.B, lb = line % ps.B;
+  const int e0 = blockIdx.y * FFT_EC;
+  const int ec = min(FFT_EC, E - e0);
+  const int n = ps.n;
+  const bool pow2 = (n & (n - 1)) == 0;
+  const int logn = 31 - __clz(n);
+  for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
+    const int j = idx / FFT_EC, e = idx % FFT_EC;
+    if (e >= ec) continue;
+    const long slot = ((long)la * n + j) * ps.B + lb;
+    double2 v;
+    if (xin) {
+      v.x = xin[slot * 2 * E + e0 + e];
+      v.y = xin[slot * 2 * E + E + e0 + e];
+    } else {
+      v = cin[slot * E + e0 + e];
+    }
+    const int jj = (pow2 && n > 1) ? bitrev(j, logn) : j;
+    sbuf[jj * FFT_EC + e] = v;
+  }
+  __syncthreads();
+  const double2* Wn = tw + ps.w_off;  // exp(-2 pi i t / n)
+  const double2* res = sbuf;
+  if (pow2) {
+    for (int half = 1; half < n; half <<= 1) {
+      const int stride = n / (2 * half);
+      for (int idx = threadIdx.x; idx < (n / 2) * FFT_EC; idx += FFT_THREADS) {
+        const int e = idx % FFT_EC, bf = idx / FFT_EC;
+        const int grp = bf / half, j = bf % half;
+        const int i0 = grp * 2 * half + j, i1 = i0 + half;
+        double2 w = Wn[j * stride];
+        if (dir > 0) w.y = -w.y;
+        const double2 u = sbuf[i0 * FFT_EC + e];
+        const double2 t = cmul(w, sbuf[i1 * FFT_EC + e]);
+        sbuf[i0 * FFT_EC + e] = make_double2(u.x + t.x, u.y + t.y);
+        sbuf[i1 * FFT_EC + e] = make_double2(u.x - t.x, u.y - t.y);
+      }
+      __syncthreads();
+    }
+  } else {
+    double2* obuf = sbuf + n * FFT_EC;
+    for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
+      const int k = idx / FFT_EC, e = idx % FFT_EC;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int j = 0; j < n; ++j) {
+        double2 w = Wn[(j * k) % n];
+        if (dir > 0) w.y = -w.y;
+        const double2 t = cmul(w, sbuf[j * FFT_EC + e]);
+        acc.x += t.x;
+        acc.y += t.y;
+      }
+      obuf[idx] = acc;
+    }
+    __syncthreads();
+    res = obuf;
+  }
+  for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
+    const int k = idx / FFT_EC, e = idx % FFT_EC;
+    if (e >= ec) continue;
+    double2 v = res[idx];
+    if (ps.tw_mode) {
+      const int other = (ps.tw_mode == 1) ? lb : la;
+      double2 w = tw[ps.tw_off + (int)(((long)k * other) % ps.twN)];
+      if (dir > 0) w.y = -w.y;
+      v = cmul(v, w);
+    }
+    const long slot = ((long)la * n + k) * ps.B + lb;
+    if (xout) {
+      xout[slot * 2 * E + e0 + e] = v.x;
+      xout[slot * 2 * E + E + e0 + e] = v.y;
+    } else {
+      cout[slot * E + e0 + e] = v;
+    }
+  }
+}
+
+__global__ void k_fft_tables(double2* tw, const FftPlan p) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p.ntw; t += gridDim.x * blockDim.x) {
+    int tab = 0;
+    while (tab + 1 < p.ntab && t >= p.tab_off[tab + 1]) ++tab;
+    const int n = p.tab_n[tab], j = t - p.tab_off[tab];
+    double s, c;
+    sincospi(2.0 * (double)j / (double)n, &s, &c);
+    tw[t] = make_double2(c, -s);
+  }
+}
+
+// Slot of -k for the spectrum slot s (see the layout notes at the top of the file).
+__device__ __forceinline__ int partner_slot(const FftPlan& p, int s) {
+  if (p.dim == 2) {
+    const int k0 = s / p.M1, k1 = s % p.M1;
+    return ((p.M0 - k0) % p.M0) * p.M1 + (p.M1 - k1) % p.M1;
+  }
+  if (p.npass == 1) return (p.N - s) % p.N;
+  const int c = s / p.N2, e = s % p.N2;
+  const int k = c + p.N1 * e;
+  const int kk = (p.N - k) % p.N;
+  return (kk % p.N1) * p.N2 + kk / p.N1;
+}
+
+template <int D, typename T>
+struct XSmem {
+  static constexpr int LD = GroupShape<D>::LD;
+  static constexpr size_t MAT = ((sizeof(T) * D * LD + 15) / 16) * 16;
+  static constexpr size_t bytes = 4 * MAT + ((sizeof(T) * 2 * D + 15) / 16) * 16 +
+                                  ((sizeof(T) * D + 15) / 16) * 16 + 16 * sizeof(T);
+};
+
+// Unpack block C_k (unnormalised) of slot s from the packed spectrum into (Ar, Ai), Hermitised.
+template <int D, int NT, int LD, typename T>
+__device__ void unpack_block(const double2* spec, int s, int s2, int E, T* Ar, T* Ai, int tid) {
+  for (int f = tid; f < D * D; f += NT) {
+    const int e = f < E ? f : f - E;
+    const double2 z = spec[(long)s * E + e];
+    const double2 zz = spec[(long)s2 * E + e];  // conj taken below
+    double cr, ci;
+    if (f < E) {  // (z + conj(zz)) / 2
+      cr = 0.5 * (z.x + zz.x);
+      ci = 0.5 * (z.y - zz.y);
+    } else {      // (z - conj(zz)) / (2i)
+      const double dr = z.x - zz.x, di = z.y + zz.y;
+      cr = 0.5 * di;
+      ci = -0.5 * dr;
+    }
+    Ar[(f / D) * LD + (f % D)] = (T)cr;
+    Ai[(f / D) * LD + (f % D)] = (T)ci;
+  }
+  gsync<NT>();
+  for (int f = tid; f < D * D; f += NT) {
+    const int i = f / D, j = f % D;
+    if (i < j) {
+      const T r = T(0.5) * (Ar[i * LD + j] + Ar[j * LD + i]);
+      const T im = T(0.5) * (Ai[i * LD + j] - Ai[j * LD + i]);
+      Ar[i * LD + j] = r;
+      Ai[i * LD + j] = im;
+      Ar[j * LD + i] = r;
+      Ai[j * LD + i] = -im;
+    } else if (i == j) {
+      Ai[i * LD + i] = T(0);
+    }
+  }
+  gsync<NT>();
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
+    k_xproj(double2* spec, const FftPlan p, const double invN) {
+  constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
+  constexpr int GPC = (NT == 32) ? 4 : 1;
+  using S = XSmem<D, T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
+  unsigned char* base = smem_raw + (size_t)g * S::bytes;
+  T* Ar = reinterpret_cast<T*>(base);
+  T* Ai = reinterpret_cast<T*>(base + S::MAT);
+  T* Vr = reinterpret_cast<T*>(base + 2 * S::MAT);
+  T* Vi = reinterpret_cast<T*>(base + 3 * S::MAT);
+  T* cs = reinterpret_cast<T*>(base + 4 * S::MAT);
+  T* W = cs + 2 * D;
+  T* red = W + D;
+  const int E = p.E;
+  for (int s = blockIdx.x * GPC + g; s < p.N; s += gridDim.x * GPC) {
+    const int s2 = partner_slot(p, s);
+    if (s2 < s) continue;
+    unpack_block<D, NT, LD, T>(spec, s, s2, E, Ar, Ai, tid);
+    jacobi_herm<T, D, LD, NT, true>(Ar, Ai, Vr, Vi, cs, red, tid);
+    for (int k = tid; k < D; k += NT) {
+      const T w = Ar[k * LD + k];
+      W[k] = w > T(0) ? w : T(0);
+    }
+    gsync<NT>();
+    // Y = V diag(max(w,0)) V^H, written back into (Ar, Ai)
+    for (int f = tid; f < D * D; f += NT) {
+      const int i = f / D, j = f % D;
+      if (i <= j) {
+        T yr = T(0), yi = T(0);
+        for (int k = 0; k < D; ++k) {
+          const T w = W[k];
+          const T air = Vr[i * LD + k], aii = Vi[i * LD + k];
+          const T ajr = Vr[j * LD + k], aji = Vi[j * LD + k];
+          yr += w * (air * ajr + aii * aji);
+          yi += w * (aii * ajr - air * aji);
+        }
+        Ar[i * LD + j] = yr;
+        Ai[i * LD + j] = yi;
+        Ar[j * LD + i] = yr;
+        Ai[j * LD + i] = -yi;
+      }
+    }
+    gsync<NT>();
+    // pack Y_k (and Y_{-k} = conj Y_k) back, scaled by 1/N
+    for (int e = tid; e < E; e += NT) {
+      const int f1 = e, f2 = e + E;
+      const double y1r = (double)Ar[(f1 / D) * LD + f1 % D] * invN;
+      const double y1i = (double)Ai[(f1 / D) * LD + f1 % D] * invN;
+      const double y2r = (double)Ar[(f2 / D) * LD + f2 % D] * invN;
+      const double y2i = (double)Ai[(f2 / D) * LD + f2 % D] * invN;
+      spec[(long)s * E + e] = make_double2(y1r - y2i, y1i + y2r);
+      if (s2 != s) spec[(long)s2 * E + e] = make_double2(y1r + y2i, -y1i + y2r);
+    }
+    gsync<NT>();
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
+    k_xeig(const double2* spec, const FftPlan p, double* lmin) {
+  constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
+  constexpr int GPC = (NT == 32) ? 4 : 1;
+  using S = XSmem<D, double>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
+  unsigned char* base = smem_raw + (size_t)g * S::bytes;
+  double* Ar = reinterpret_cast<double*>(base);
+  double* Ai = reinterpret_cast<double*>(base + S::MAT);
+  double* cs = reinterpret_cast<double*>(base + 4 * S::MAT);
+  double* red = cs + 3 * D;
+  for (int s = blockIdx.x * GPC + g; s < p.N; s += gridDim.x * GPC) {
+    const int s2 = partner_slot(p, s);
+    if (s2 < s) {
+      if (tid == 0) lmin[s] = INFINITY;
+      continue;
+    }
+    unpack_block<D, NT, LD, double>(spec, s, s2, p.E, Ar, Ai, tid);
+    jacobi_herm<double, D, LD, NT, false>(Ar, Ai, nullptr, nullptr, cs, red, tid);
+    double w = INFINITY;
+    for (int k = tid; k < D; k += NT) w = fmin(w, Ar[k * LD + k]);
+    w = gmin<NT>(w, red);
+    if (tid == 0) lmin[s] = w;
+    gsync<NT>();
+  }
+}
+
+
+template <int D, typename T>
+cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, cudaStream_t s) {
+  constexpr int NT = GroupShape<D>::NT, GPC = (NT == 32) ? 4 : 1;
+  const size_t smem = XSmem<D, T>::bytes * GPC;
+  static unsigned long long mask = 0;
+  cudaError_t e = smem_once(k_xproj<D, T>, smem, mask);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((p.N + GPC - 1) / GPC);
+  k_xproj<D, T><<<blocks, NT * GPC, smem, s>>>(spec, p, 1.0 / p.N);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_xeig_t(const FftPlan& p, const double2* spec, double* lmin, cudaStream_t s) {
+  constexpr int NT = GroupShape<D>::NT, GPC = (NT == 32) ? 4 : 1;
+  const size_t smem = XSmem<D, double>::bytes * GPC;
+  static unsigned long long mask = 0;
+  cudaError_t e = smem_once(k_xeig<D>, smem, mask);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((p.N + GPC - 1) / GPC);
+  k_xeig<D><<<blocks, NT * GPC, smem, s>>>(spec, p, lmin);
+  return cudaGetLastError();
+}
+
+cudaError_t run_pass(const FftPlan& p, const FftPass& ps, int dir, const double* xin,
+                     const double2* cin, double2* cout, double* xout, const double2* tw,
+                     cudaStream_t s) {
+  const bool pow2 = (ps.n & (ps.n - 1)) == 0;
+  const size_t smem = sizeof(double2) * ps.n * FFT_EC * (pow2 ? 1 : 2);
+  static unsigned long long mask = 0;
+  cudaError_t e = smem_once(k_fft_pass, 2 * sizeof(double2) * 64 * FFT_EC, mask);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(ps.A * ps.B), (unsigned)((p.E + FFT_EC - 1) / FFT_EC));
+  k_fft_pass<<<grid, FFT_THREADS, smem, s>>>(xin, cin, cout, xout, ps, dir, p.E, tw);
+  return cudaGetLastError();
+}
+
+int smallest_factor_pair(int N, int& N1, int& N2) {
+  // N = N1 * N2 with N1 >= N2, both <= 64, preferring the most balanced split
+  int best = -1;
+  for (int a = 1; a <= 64; ++a) {
+    if (N % a) continue;
+    const int b = N / a;
+    if (b > 64 || a < b) continue;
+    if (best < 0 || a < best) best = a;
+  }
+  if (best < 0) return -1;
+  N1 = best;
+  N2 = N / best;
+  return 0;
+}
+
+}  // namespace
+
+int fft_plan_build(FftPlan& p, int dim, const int M[2], int D) {
+  p = FftPlan{};
+  p.dim = dim;
+  p.D = D;
+  p.E = D * D / 2;
+  if (dim == 1) {
+    p.M0 = M[0];
+    p.M1 = 1;
+    p.N = M[0];
+    if (p.N < 2) return VE_EINVAL;
+    if (p.N <= 64) {
+      p.npass = 1;
+      p.N1 = p.N;
+      p.N2 = 1;
+      p.ntab = 1;
+      p.tab_n[0] = p.N;
+      p.tab_off[0] = 0;
+      p.ntw = p.N;
+      p.fwd[0] = FftPass{1, p.N, 1, 0, 1, 0, 0};
+      p.inv[0] = p.fwd[0];
+    } else {
+      int N1, N2;
+      if (p.N > 4096 || smallest_factor_pair(p.N, N1, N2)) return VE_EUNSUPPORTED;
+      p.npass = 2;
+      p.N1 = N1;
+      p.N2 = N2;
+      p.ntab = 3;
+      p.tab_n[0] = N1;
+      p.tab_n[1] = N2;
+      p.tab_n[2] = p.N;
+      p.tab_off[0] = 0;
+      p.tab_off[1] = N1;
+      p.tab_off[2] = N1 + N2;
+      p.ntw = N1 + N2 + p.N;
+      // forward: along a (length N1, lines b), twiddle w_N^(c b); then along b (length N2, lines c)
+      p.fwd[0] = FftPass{1, N1, N2, 1, p.N, p.tab_off[0], p.tab_off[2]};
+      p.fwd[1] = FftPass{N1, N2, 1, 0, 1, p.tab_off[1], 0};
+      // inverse: along e (length N2, lines c) with twiddle w_N^(-b c); then along c (lines b)
+      p.inv[0] = FftPass{N1, N2, 1, 2, p.N, p.tab_off[1], p.tab_off[2]};
+      p.inv[1] = FftPass{1, N1, N2, 0, 1, p.tab_off[0], 0};
+    }
+  } else if (dim == 2) {
+    p.M0 = M[0];
+    p.M1 = M[1];
+    p.N = M[0] * M[1];
+    if (p.M0 < 1 || p.M1 < 1 || p.N < 2) return VE_EINVAL;
+    if (p.M0 > 64 || p.M1 > 64) return VE_EUNSUPPORTED;
+    p.npass = 2;
+    p.N1 = p.M0;
+    p.N2 = p.M1;
+    p.ntab = 2;
+    p.tab_n[0] = p.M0;
+    p.tab_n[1] = p.M1;
+    p.tab_off[0] = 0;
+    p.tab_off[1] = p.M0;
+    p.ntw = p.M0 + p.M1;
+    p.fwd[0] = FftPass{1, p.M0, p.M1, 0, 1, p.tab_off[0], 0};
+    p.fwd[1] = FftPass{p.M0, p.M1, 1, 0, 1, p.tab_off[1], 0};
+    p.inv[0] = p.fwd[1];
+    p.inv[1] = p.fwd[0];
+  } else {
+    return VE_EINVAL;
+  }
+  if (D != 4 && D != 16 && D != 64) return VE_EUNSUPPORTED;
+  return 0;
+}
+
+cudaError_t launch_fft_tables(const FftPlan& p, double2* tw, cudaStream_t s) {
+  k_fft_tables<<<(p.ntw + 255) / 256, 256, 0, s>>>(tw, p);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_forward(const FftPlan& p, const double* x, double2* bufA, double2* bufB,
+                        const double2* tw, double2** spec, cudaStream_t s) {
+  cudaError_t e = run_pass(p, p.fwd[0], -1, x, nullptr, bufA, nullptr, tw, s);
+  if (e != cudaSuccess) return e;
+  if (p.npass == 1) {
+    *spec = bufA;
+    return cudaSuccess;
+  }
+  e = run_pass(p, p.fwd[1], -1, nullptr, bufA, bufB, nullptr, tw, s);
+  *spec = bufB;
+  return e;
+}
+
+cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2* bufB, double* x,
+                        const double2* tw, cudaStream_t s) {
+  if (p.npass == 1) return run_pass(p, p.inv[0], +1, nullptr, spec, nullptr, x, tw, s);
+  double2* other = (spec == bufA) ? bufB : bufA;
+  cudaError_t e = run_pass(p, p.inv[0], +1, nullptr, spec, other, nullptr, tw, s);
+  if (e != cudaSuccess) return e;
+  return run_pass(p, p.inv[1], +1, nullptr, other, nullptr, x, tw, s);
+}
+
+cudaError_t launch_xproj(const FftPlan& p, double2* spec, bool fp32, cudaStream_t s) {
+  switch (p.D) {
+    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, s) : launch_xproj_t<4, double>(p, spec, s);
+    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, s) : launch_xproj_t<16, double>(p, spec, s);
+    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, s) : launch_xproj_t<64, double>(p, spec, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_xeig(const FftPlan& p, const double2* spec, double* lmin, cudaStream_t s) {
+  switch (p.D) {
+    case 4: return launch_xeig_t<4>(p, spec, lmin, s);
+    case 16: return launch_xeig_t<16>(p, spec, lmin, s);
+    case 64: return launch_xeig_t<64>(p, spec, lmin, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ve

@@ -1,0 +1,124 @@
+// ve_internal.h -- declarations shared by the solver's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace ve {
+
+// Raise a kernel's dynamic shared-memory limit once per device (outside any stream capture:
+// the first sweep of a handle runs uncaptured).
+template <typename K>
+inline cudaError_t smem_once(K kernel, size_t bytes, unsigned long long& mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (mask & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes);
+  if (e == cudaSuccess) mask |= bit;
+  return e;
+}
+
+// ------------------------------------------------------------------ sweep kernels
+struct PairArgs {
+  int N, P, m, D;
+  double mu, nu, eps;
+  const double* rho0;   // m*m
+  double* rt;           // P*D*D   rho~ (read, then overwritten)
+  double* lam;          // P*D*D   Lambda
+  const double* lam1;   // P*m*m
+  const double* lam2;   // P*m*m
+  double* X;            // N*D*D   X_{0,delta}; blocks 1..N-1 become X' in the pair pass
+  const double* hb;     // nonzero pair Hamiltonian blocks, D*D each
+  const int* hslot;     // per linear delta: index into hb or -1
+  double* a1r;          // P*m*m   A1[rho_{0,delta}]
+  double* a2r;          // P*m*m   A2[rho_{0,delta}]
+  double* part;         // P*2     ||rho - rho~||^2, Tr[H rho]
+};
+
+struct DevStatus {
+  long long iter;
+  double energy, feas, d_energy, residual;
+  double e_prev;
+  double h0rho0;  // Tr[H_0 rho_0] of the current sweep
+  double pad;
+};
+
+struct SmallArgs {
+  int N, P, m, D, L;
+  double mu, nu, eps;
+  double* rho0;
+  double* lam1;
+  double* lam2;
+  double* X;
+  const double* H0;
+  const double* a1r;
+  const double* a2r;
+  const double* part;
+  double* part2;  // P: ||A1 rho - rho0||^2 + ||A2 rho - rho0||^2
+  DevStatus* st;
+};
+
+// D in {4, 16, 64}; fp32 selects the float32 projection.
+cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s);
+cudaError_t launch_rho0(const SmallArgs& a, cudaStream_t s);
+cudaError_t launch_dual12(const SmallArgs& a, cudaStream_t s);
+cudaError_t launch_status(const SmallArgs& a, cudaStream_t s);
+
+// ------------------------------------------------------------------ block DFT over delta
+// The first block row is viewed as a row-major array [A][n][B] of slots (delta, or wavevector
+// after the forward passes), each slot holding E = D*D/2 complex values: entry e of slot t is
+// X_t[e] + i X_t[e + E] (two real block entries packed in one complex sequence).
+struct FftPass {
+  int A, n, B;
+  int tw_mode;  // 0: none; 1: times w_twN^(dir*k*b); 2: times w_twN^(dir*k*a)  (k = output index)
+  int twN;
+  int w_off;    // offset of the length-n table exp(-2 pi i j / n) in the twiddle buffer
+  int tw_off;   // offset of the length-twN table
+};
+
+struct FftPlan {
+  int dim, M0, M1, N, N1, N2, E, D, npass;
+  FftPass fwd[2], inv[2];
+  int ntab;
+  int tab_n[3], tab_off[3];
+  int ntw;  // total twiddle entries
+};
+
+// Returns 0, or VE_EUNSUPPORTED / VE_EINVAL codes.
+int fft_plan_build(FftPlan& p, int dim, const int M[2], int D);
+cudaError_t launch_fft_tables(const FftPlan& p, double2* tw, cudaStream_t s);
+// Forward: real first block row x (N*D*D) -> spectrum (returned pointer is bufA or bufB).
+cudaError_t fft_forward(const FftPlan& p, const double* x, double2* bufA, double2* bufB,
+                        const double2* tw, double2** spec, cudaStream_t s);
+// Inverse: spectrum (in `spec`, which is bufA or bufB) -> real first block row x.
+cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2* bufB, double* x,
+                        const double2* tw, cudaStream_t s);
+// Per-wavevector projection in place on the spectrum, scaled by 1/N.
+cudaError_t launch_xproj(const FftPlan& p, double2* spec, bool fp32, cudaStream_t s);
+// lmin[slot] = smallest eigenvalue of the (unnormalised) block C_k, +inf for non-canonical slots.
+cudaError_t launch_xeig(const FftPlan& p, const double2* spec, double* lmin, cudaStream_t s);
+
+// ------------------------------------------------------------------ bound
+struct BoundArgs {
+  int N, P, m, D;
+  const double* X;
+  const double* lam1;
+  const double* hb;
+  const int* hslot;
+  const int* neg;       // linear index of -delta
+  const double* H0;
+  double* lmin_pairs;   // P
+  double* lmin0;        // 1
+};
+cudaError_t launch_bound(const BoundArgs& a, cudaStream_t s);
+
+// ------------------------------------------------------------------ standalone projections
+cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, bool fp32,
+                            cudaStream_t s);
+cudaError_t launch_proj_herm(const double* in, double* out, int n, long count, bool fp32,
+                             cudaStream_t s);
+
+}  // namespace ve

@@ -1,0 +1,321 @@
+// ve_sweep.cu -- the pair pass and the small reductions of one sweep of Algorithm 6
+// (Khoo & Lindsey, arXiv:2106.02682, Sec. 3.3).
+//
+// k_pair     : one thread group per pair offset delta != 0.  Fuses the effective pair
+//              Hamiltonian (Eq. (effHam)), the closed-form pair update (Eq. (rhoijUpdate)),
+//              the PSD projection (Eq. (rhoijTildeUpdate)), the Lambda update, the X' = X - eps G
+//              step for the block (Algorithm 6), the partial traces A1 rho, A2 rho and the
+//              per-delta terms of Eq. (feasErr) and of the energy.
+// k_rho0     : one CTA.  rho_0 update (Eq. (rhoiUpdate), translation-invariant form) with the
+//              trace shift, and X'_00 = X_00 - eps G_00[rho_0].
+// k_dual12   : Lambda1/Lambda2 updates (they need the new rho_0) and their feasibility terms.
+// k_status   : one CTA.  Energy per spin, Eq. (feasErr), |energy change|, residual.
+// All reductions run in a fixed order, so a sweep is bitwise reproducible.
+#include "ve_device.cuh"
+#include "ve_internal.h"
+
+namespace ve {
+
+namespace {
+
+template <int D>
+struct PairShape {
+  static constexpr int m = (D == 4) ? 2 : (D == 16) ? 4 : 8;
+  static constexpr int NT = GroupShape<D>::NT;
+  static constexpr int LD = GroupShape<D>::LD;
+  static constexpr int GPC = (NT == 32) ? 4 : 1;  // groups per CTA
+};
+
+template <int D, typename T>
+struct PairSmem {
+  static constexpr int m = PairShape<D>::m, LD = PairShape<D>::LD;
+  // per group, in bytes; every array 16-byte aligned
+  static constexpr size_t R = 0;                                      // double D*D
+  static constexpr size_t Xs = R + sizeof(double) * D * D;           // double D*D
+  static constexpr size_t A = Xs + sizeof(double) * D * D;           // T D*LD
+  static constexpr size_t V = A + ((sizeof(T) * D * LD + 15) / 16) * 16;
+  static constexpr size_t CS = V + ((sizeof(T) * D * LD + 15) / 16) * 16;  // T D
+  static constexpr size_t W = CS + ((sizeof(T) * D + 15) / 16) * 16;       // T D
+  static constexpr size_t TR = W + ((sizeof(T) * D + 15) / 16) * 16;       // double 2*m*m + 2
+  static constexpr size_t RED = TR + ((sizeof(double) * (2 * m * m + 2) + 15) / 16) * 16;
+  static constexpr size_t REDT = RED + sizeof(double) * 8;
+  static constexpr size_t bytes = REDT + ((sizeof(T) * 8 + 15) / 16) * 16;
+};
+
+template <int D, typename T>
+__global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
+    k_pair(const PairArgs a) {
+  constexpr int m = PairShape<D>::m, NT = PairShape<D>::NT, LD = PairShape<D>::LD;
+  constexpr int GPC = PairShape<D>::GPC;
+  using S = PairSmem<D, T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
+  unsigned char* base = smem_raw + (size_t)g * S::bytes;
+  double* R = reinterpret_cast<double*>(base + S::R);
+  double* Xs = reinterpret_cast<double*>(base + S::Xs);
+  T* A = reinterpret_cast<T*>(base + S::A);
+  T* V = reinterpret_cast<T*>(base + S::V);
+  T* cs = reinterpret_cast<T*>(base + S::CS);
+  T* W = reinterpret_cast<T*>(base + S::W);
+  double* t1 = reinterpret_cast<double*>(base + S::TR);
+  double* t2 = t1 + m * m;
+  double* red = reinterpret_cast<double*>(base + S::RED);
+  T* redT = reinterpret_cast<T*>(base + S::REDT);
+
+  const double mu = a.mu, nu = a.nu, eps = a.eps;
+  const double alpha = nu * m;
+  const double c0 = 1.0 / mu, c1 = 1.0 / (mu + alpha), c2 = 1.0 / (mu + 2.0 * alpha);
+
+  for (long p = (long)blockIdx.x * GPC + g; p < a.P; p += (long)gridDim.x * GPC) {
+    const long dl = p + 1;  // linear cluster offset delta
+    const double* rt = a.rt + p * D * D;
+    const double* lam = a.lam + p * D * D;
+    const double* l1 = a.lam1 + p * m * m;
+    const double* l2 = a.lam2 + p * m * m;
+    double* Xb = a.X + dl * D * D;
+    const int hs = a.hslot[dl];
+    const double* Hb = hs >= 0 ? a.hb + (long)hs * D * D : nullptr;
+
+    for (int e = tid; e < D * D; e += NT) Xs[e] = Xb[e];
+    gsync<NT>();
+    // right-hand side of Eq. (rhoijUpdate) with H' of Eq. (effHam)
+    for (int e = tid; e < D * D; e += NT) {
+      const int i = e / D, j = e % D;
+      const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+      const double h = Hb ? Hb[e] : 0.0;
+      // (R^* X)_{(a,b),(c,d)} = X_{(a,c),(d,b)} and its transpose X_{(c,a),(b,d)}
+      const double hp = h - Xs[(pa * m + pc) * D + (pd * m + pb)] - Xs[(pc * m + pa) * D + (pb * m + pd)];
+      double y = mu * rt[e] + lam[e] - hp;
+      if (pb == pd) y += nu * a.rho0[pa * m + pc] - l1[pa * m + pc];
+      if (pa == pc) y += nu * a.rho0[pb * m + pd] - l2[pb * m + pd];
+      R[e] = y;
+    }
+    gsync<NT>();
+    // partial traces of the right-hand side
+    for (int idx = tid; idx < m * m; idx += NT) {
+      const int x = idx / m, z = idx % m;
+      double s1 = 0.0, s2 = 0.0;
+      for (int k = 0; k < m; ++k) {
+        s1 += R[(x * m + k) * D + (z * m + k)];
+        s2 += R[(k * m + x) * D + (k * m + z)];
+      }
+      t1[idx] = s1;
+      t2[idx] = s2;
+    }
+    gsync<NT>();
+    double tr = 0.0;
+    for (int k = 0; k < m; ++k) tr += t1[k * m + k];
+    // rho = (mu + nu A1^*A1 + nu A2^*A2)^{-1} rhs, closed form on the projectors P1, P2, Q
+    for (int e = tid; e < D * D; e += NT) {
+      const int i = e / D, j = e % D;
+      const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+      const double y = R[e];
+      const double P1 = (pb == pd) ? t1[pa * m + pc] / m : 0.0;
+      const double P2 = (pa == pc) ? t2[pb * m + pd] / m : 0.0;
+      const double Q = (i == j) ? tr / D : 0.0;
+      R[e] = (y - P1 - P2 + Q) * c0 + (P1 + P2 - 2.0 * Q) * c1 + Q * c2;
+    }
+    gsync<NT>();
+    // C = rho - Lambda / mu, symmetrised, into A
+    for (int e = tid; e < D * D; e += NT) {
+      const int i = e / D, j = e % D;
+      if (i <= j) {
+        const double v = 0.5 * (R[i * D + j] + R[j * D + i]) - 0.5 * (lam[i * D + j] + lam[j * D + i]) / mu;
+        A[i * LD + j] = (T)v;
+        A[j * LD + i] = (T)v;
+      }
+    }
+    gsync<NT>();
+    jacobi_sym<T, D, LD, NT, true>(A, V, cs, redT, tid);
+    for (int k = tid; k < D; k += NT) {
+      const T w = A[k * LD + k];
+      W[k] = w > T(0) ? w : T(0);
+    }
+    gsync<NT>();
+    // rho~ = V diag(max(w, 0)) V^T
+    for (int e = tid; e < D * D; e += NT) {
+      const int i = e / D, j = e % D;
+      if (i <= j) {
+        T s = T(0);
+#pragma unroll 4
+        for (int k = 0; k < D; ++k) s += W[k] * V[i * LD + k] * V[j * LD + k];
+        A[i * LD + j] = s;
+        A[j * LD + i] = s;
+      }
+    }
+    gsync<NT>();
+    double rr = 0.0, en = 0.0;
+    double* rtw = a.rt + p * D * D;
+    double* lamw = a.lam + p * D * D;
+    for (int e = tid; e < D * D; e += NT) {
+      const int i = e / D, j = e % D;
+      const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+      const double rho = R[e];
+      const double rtn = (double)A[i * LD + j];
+      const double h = Hb ? Hb[e] : 0.0;
+      lamw[e] = lam[e] + mu * (rtn - rho);
+      rtw[e] = rtn;
+      // X'_{0,delta} = X_{0,delta} - eps G_{0,delta}[rho], G entry (a,b),(c,d) = rho_{(a,d),(b,c)}
+      Xb[e] = Xs[e] - eps * R[(pa * m + pd) * D + (pb * m + pc)];
+      rr += (rho - rtn) * (rho - rtn);
+      en += h * R[j * D + i];
+    }
+    for (int idx = tid; idx < m * m; idx += NT) {
+      const int x = idx / m, z = idx % m;
+      double s1 = 0.0, s2 = 0.0;
+      for (int k = 0; k < m; ++k) {
+        s1 += R[(x * m + k) * D + (z * m + k)];
+        s2 += R[(k * m + x) * D + (k * m + z)];
+      }
+      a.a1r[p * m * m + idx] = s1;
+      a.a2r[p * m * m + idx] = s2;
+    }
+    rr = gsum<NT>(rr, red);
+    en = gsum<NT>(en, red);
+    if (tid == 0) {
+      a.part[p * 2 + 0] = rr;
+      a.part[p * 2 + 1] = en;
+    }
+    gsync<NT>();
+  }
+}
+
+template <int D, typename T>
+cudaError_t launch_pair_t(const PairArgs& a, cudaStream_t s) {
+  constexpr int NT = PairShape<D>::NT, GPC = PairShape<D>::GPC;
+  const size_t smem = PairSmem<D, T>::bytes * GPC;
+  static unsigned long long mask = 0;
+  cudaError_t e = smem_once(k_pair<D, T>, smem, mask);
+  if (e != cudaSuccess) return e;
+  long blocks = (a.P + GPC - 1) / GPC;
+  if (blocks < 1) blocks = 1;
+  k_pair<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- rho_0 and X'_00 (one CTA)
+__global__ void __launch_bounds__(256) k_rho0(const SmallArgs a) {
+  __shared__ double S[256];
+  __shared__ double rp[64];
+  __shared__ double red[8];
+  const int m = a.m, mm = m * m, D = a.D, P = a.P;
+  const int t = threadIdx.x;
+  const int chunks = 256 / mm;  // m*m in {4, 16, 64}
+  // sum_delta (nu A1[rho_{0,delta}] + Lambda1_{0,delta}), chunked over delta in fixed order
+  if (t < chunks * mm) {
+    const int idx = t % mm, c = t / mm;
+    const long per = (P + chunks - 1) / chunks;
+    const long lo = c * per, hi = min((long)P, lo + per);
+    double s = 0.0;
+    for (long p = lo; p < hi; ++p) s += a.nu * a.a1r[p * mm + idx] + a.lam1[p * mm + idx];
+    S[t] = s;
+  }
+  __syncthreads();
+  if (t < mm) {
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += S[c * mm + t];
+    // H'_0 = H_0 - sum_a X_{(a,b),(a,d)}  (Eq. (effHam) with matrix units)
+    const int b = t / m, d = t % m;
+    double hx = 0.0;
+    for (int x = 0; x < m; ++x) hx += a.X[(x * m + b) * D + (x * m + d)];
+    const double h0p = a.H0[t] - hx;
+    rp[t] = (s - h0p) / (a.nu * (a.N - 1));
+  }
+  __syncthreads();
+  double tr = 0.0;
+  for (int k = 0; k < m; ++k) tr += rp[k * m + k];
+  const double z = (1.0 - tr) / m;
+  if (t < mm) {
+    const int b = t / m, d = t % m;
+    rp[t] = rp[t] + (b == d ? z : 0.0);
+  }
+  __syncthreads();
+  if (t < mm) a.rho0[t] = rp[t];
+  // X'_00 = X_00 - eps G_00[rho_0], G_00 entry (a,b),(c,d) = delta_ac rho0_{d,b}
+  for (int e = t; e < D * D; e += 256) {
+    const int i = e / D, j = e % D;
+    const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+    if (pa == pc) a.X[e] -= a.eps * rp[pd * m + pb];
+  }
+  // Tr[H_0 rho_0]
+  double h = 0.0;
+  if (t < mm) h = a.H0[t] * rp[(t % m) * m + (t / m)];
+  h = gsum<256>(h, red);
+  if (t == 0) a.st->h0rho0 = h;
+}
+
+// ---------------------------------------------------------------- Lambda1, Lambda2
+__global__ void k_dual12(const SmallArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int mm = a.m * a.m;
+  if (w >= a.P) return;
+  double s = 0.0;
+  for (int idx = lane; idx < mm; idx += 32) {
+    const double r0 = a.rho0[idx];
+    const double d1 = a.a1r[w * mm + idx] - r0;
+    const double d2 = a.a2r[w * mm + idx] - r0;
+    a.lam1[w * mm + idx] += a.nu * d1;
+    a.lam2[w * mm + idx] += a.nu * d2;
+    s += d1 * d1 + d2 * d2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) a.part2[w] = s;
+}
+
+// ---------------------------------------------------------------- status (one CTA)
+__global__ void __launch_bounds__(256) k_status(const SmallArgs a) {
+  __shared__ double red[8];
+  double rr = 0.0, en = 0.0, ff = 0.0;
+  for (long p = threadIdx.x; p < a.P; p += 256) {
+    rr += a.part[p * 2 + 0];
+    en += a.part[p * 2 + 1];
+    ff += a.part2[p];
+  }
+  rr = gsum<256>(rr, red);
+  en = gsum<256>(en, red);
+  ff = gsum<256>(ff, red);
+  if (threadIdx.x == 0) {
+    DevStatus* st = a.st;
+    const double E = (st->h0rho0 + 0.5 * en) / a.L;
+    const double feas = sqrt((rr + ff) / a.P);
+    const double dE = isfinite(st->e_prev) ? fabs(E - st->e_prev) : INFINITY;
+    st->energy = E;
+    st->feas = feas;
+    st->d_energy = dE;
+    st->residual = fmax(feas, dE);
+    st->e_prev = E;
+    st->iter += 1;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s) {
+  switch (a.D) {
+    case 4: return fp32 ? launch_pair_t<4, float>(a, s) : launch_pair_t<4, double>(a, s);
+    case 16: return fp32 ? launch_pair_t<16, float>(a, s) : launch_pair_t<16, double>(a, s);
+    case 64: return fp32 ? launch_pair_t<64, float>(a, s) : launch_pair_t<64, double>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_rho0(const SmallArgs& a, cudaStream_t s) {
+  k_rho0<<<1, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dual12(const SmallArgs& a, cudaStream_t s) {
+  const long threads = (long)a.P * 32;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  k_dual12<<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_status(const SmallArgs& a, cudaStream_t s) {
+  k_status<<<1, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ve

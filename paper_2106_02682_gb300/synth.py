@@ -1,0 +1,77 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the CPU oracle's callers.
+
+Only random-matrix and workload generators live here (no step of the solver's arithmetic):
+  * symmetric_batch / hermitian_batch: matrices shaped like the projection inputs
+    rho - Lambda/mu and the wavevector blocks -- O(1) entries, eigenvalues of both signs, plus a
+    share with repeated eigenvalues and low rank, which stress the eigensolvers;
+  * circulant_first_row: a first block row X_{0,delta} obeying X_{0,-delta} = X_{0,delta}^T, the
+    structure of the dual matrix in Algorithm 6;
+  * workloads: the named benchmark instances (lattice, cluster, field) used by bench.py.
+The default seed is 20210604.
+"""
+import numpy as np
+
+SEED = 20210604
+
+
+def _rng(seed):
+    return np.random.default_rng(SEED if seed is None else SEED + int(seed))
+
+
+def symmetric_batch(count, n, seed=None):
+    rng = _rng(seed)
+    A = rng.normal(size=(count, n, n))
+    A = 0.5 * (A + np.swapaxes(A, 1, 2))
+    # every 7th matrix: repeated eigenvalues (+1 / -1 / 0 blocks) in a random orthogonal basis
+    for b in range(0, count, 7):
+        Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+        lam = np.repeat(np.array([1.0, -1.0, 0.0]), (n + 2) // 3)[:n]
+        A[b] = (Q * lam) @ Q.T
+    return A
+
+
+def hermitian_batch(count, n, seed=None):
+    rng = _rng(seed)
+    A = rng.normal(size=(count, n, n)) + 1j * rng.normal(size=(count, n, n))
+    A = 0.5 * (A + np.conj(np.swapaxes(A, 1, 2)))
+    for b in range(0, count, 7):
+        Z = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+        Q, _ = np.linalg.qr(Z)
+        lam = np.repeat(np.array([1.0, -1.0, 0.0]), (n + 2) // 3)[:n]
+        A[b] = (Q * lam) @ np.conj(Q.T)
+    return A
+
+
+def neg_linear_index(M):
+    """Row-major linear index of -delta for every cluster offset delta of the lattice M."""
+    M = tuple(int(x) for x in M)
+    idx = np.arange(int(np.prod(M)))
+    coords = np.array(np.unravel_index(idx, M))
+    neg = (-coords) % np.array(M)[:, None]
+    return np.ravel_multi_index(tuple(neg), M)
+
+
+def circulant_first_row(M, D, seed=None):
+    """Random N x D x D first block row with X_{0,-delta} = X_{0,delta}^T and a diagonal shift
+    that leaves the block-circulant matrix indefinite (both signs to project)."""
+    rng = _rng(seed)
+    N = int(np.prod(M))
+    X = rng.normal(size=(N, D, D)) / np.sqrt(N)
+    neg = neg_linear_index(M)
+    X = 0.5 * (X + np.swapaxes(X[neg], 1, 2))
+    X[0] += 0.1 * np.eye(D)
+    return X
+
+
+# Benchmark workloads: (name, lattice spins per axis, cluster spins per axis, field h).
+WORKLOADS = {
+    # 1-D transverse-field Ising chain, h = 1, 2-spin clusters (16 x 16 pair marginals),
+    # 4096 clusters = 4096 wavevectors (8192 spins)
+    "tfim1d_L2_N4096": dict(lattice=(8192,), cluster=(2,), h=1.0, kind="tfim"),
+    # the same chain at 4096 spins (2048 clusters)
+    "tfim1d_L2_N2048": dict(lattice=(4096,), cluster=(2,), h=1.0, kind="tfim"),
+    # 1-D TFI chain, 16 spins, single-spin clusters (4 x 4 pair marginals)
+    "tfim1d_L1_N16": dict(lattice=(16,), cluster=(1,), h=1.0, kind="tfim"),
+    # 2-D square lattice 64 x 64, h = 3, 2 x 1 clusters (16 x 16 pair marginals), 32 x 64 clusters
+    "tfim2d_L2_64x64": dict(lattice=(64, 64), cluster=(2, 1), h=3.0, kind="tfim"),
+}

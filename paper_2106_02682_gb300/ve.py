@@ -1,0 +1,263 @@
+"""ctypes binding of the C ABI in include/ve.h (argument marshalling only).
+
+Every function keeps its C name.  Status codes < 0 raise VEError; VE_OK / VE_NOT_CONVERGED are
+returned.  Device pointers are plain integers (e.g. torch_tensor.data_ptr()); streams are
+integers (torch.cuda.Stream.cuda_stream) or None.  The shared library must have been built
+(paper_2106_02682_gb300.build.build()); importing this module without it raises ImportError,
+there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libve_gb300.so")
+
+VE_OK = 0
+VE_NOT_CONVERGED = 1
+VE_EINVAL = -1
+VE_ENOMEM = -2
+VE_ECUDA = -3
+VE_ENONFINITE = -4
+VE_EUNSUPPORTED = -5
+VE_PREC_FP64 = 0
+VE_PREC_MIXED = 1
+VE_MAX_BONDS = 4
+VE_NSTAGE = 7
+STAGES = ("pair", "rho0", "dual12", "status", "fft_forward", "xproj", "fft_inverse")
+
+c_int, c_long, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_long, ctypes.c_double,
+                                               ctypes.c_void_p, ctypes.c_size_t)
+P_double = ctypes.POINTER(c_double)
+
+
+class ve_lattice(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("extent", c_int * 2)]
+
+
+class ve_cluster(ctypes.Structure):
+    _fields_ = [("extent", c_int * 2)]
+
+
+class ve_hamiltonian(ctypes.Structure):
+    _fields_ = [("onsite", c_double * 4), ("nbond", c_int),
+                ("bond_offset", (c_int * 2) * VE_MAX_BONDS),
+                ("bond", (c_double * 16) * VE_MAX_BONDS)]
+
+
+class ve_options(ctypes.Structure):
+    _fields_ = [("mu", c_double), ("nu", c_double), ("eps", c_double), ("precision", c_int),
+                ("check_every", c_int), ("stream", c_void_p)]
+
+
+class ve_status(ctypes.Structure):
+    _fields_ = [("iter", c_long), ("energy_per_spin", c_double), ("feas_err", c_double),
+                ("d_energy", c_double), ("residual", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ve_cert(ctypes.Structure):
+    _fields_ = [("bound_per_spin", c_double), ("raw_bound", c_double), ("x_min_eig", c_double),
+                ("x_neg_correction", c_double), ("primal_per_spin", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class VEError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {ve_error_string(code)} ({code})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2106_02682_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    H = c_void_p
+    sig = {
+        "ve_default_options": (None, [ctypes.POINTER(ve_options)]),
+        "ve_ham_tfim": (c_int, [c_int, c_double, c_double, ctypes.POINTER(ve_hamiltonian)]),
+        "ve_ham_xxz": (c_int, [c_int, c_double, c_double, ctypes.POINTER(ve_hamiltonian)]),
+        "ve_create": (c_int, [ctypes.POINTER(ve_lattice), ctypes.POINTER(ve_cluster),
+                              ctypes.POINTER(ve_hamiltonian), ctypes.POINTER(ve_options),
+                              ctypes.POINTER(H)]),
+        "ve_iterate": (c_int, [H, c_long, c_double, ctypes.POINTER(ve_status)]),
+        "ve_bound": (c_int, [H, ctypes.POINTER(ve_cert)]),
+        "ve_destroy": (None, [H]),
+        "ve_dims": (c_int, [H, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "ve_state_size": (c_size_t, [H]),
+        "ve_get_state": (c_int, [H, P_double, c_size_t]),
+        "ve_set_state": (c_int, [H, P_double, c_size_t]),
+        "ve_get_status": (c_int, [H, ctypes.POINTER(ve_status)]),
+        "ve_error_string": (ctypes.c_char_p, [c_int]),
+        "ve_profile": (c_int, [H, c_int]),
+        "ve_profile_read": (c_int, [H, P_double, ctypes.POINTER(c_long)]),
+        "ve_project_psd_sym": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
+        "ve_project_psd_herm": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
+        "ve_circulant_workspace_size": (c_size_t, [c_int, ctypes.POINTER(c_int), c_int]),
+        "ve_circulant_project": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(c_int), c_int,
+                                         c_int, c_void_p, c_size_t, c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+lib = _lib
+
+
+def _check(code, where):
+    if code < 0:
+        raise VEError(code, where)
+    return code
+
+
+def ve_error_string(code):
+    return _lib.ve_error_string(int(code)).decode()
+
+
+def ve_default_options(**overrides):
+    opt = ve_options()
+    _lib.ve_default_options(ctypes.byref(opt))
+    for k, v in overrides.items():
+        setattr(opt, k, v)
+    return opt
+
+
+def ve_ham_tfim(dim, J, h):
+    out = ve_hamiltonian()
+    _check(_lib.ve_ham_tfim(int(dim), float(J), float(h), ctypes.byref(out)), "ve_ham_tfim")
+    return out
+
+
+def ve_ham_xxz(dim, J, delta):
+    out = ve_hamiltonian()
+    _check(_lib.ve_ham_xxz(int(dim), float(J), float(delta), ctypes.byref(out)), "ve_ham_xxz")
+    return out
+
+
+def make_lattice(extent):
+    extent = tuple(int(e) for e in extent)
+    lat = ve_lattice()
+    lat.dim = len(extent)
+    for i, e in enumerate(extent):
+        lat.extent[i] = e
+    return lat
+
+
+def make_cluster(extent):
+    extent = tuple(int(e) for e in extent)
+    clu = ve_cluster()
+    for i, e in enumerate(extent):
+        clu.extent[i] = e
+    if len(extent) == 1:
+        clu.extent[1] = 1
+    return clu
+
+
+def ve_create(lattice, cluster, ham, opt=None):
+    """lattice / cluster: ve_lattice / ve_cluster or tuples of extents.  Returns a handle (int)."""
+    if not isinstance(lattice, ve_lattice):
+        lattice = make_lattice(lattice)
+    if not isinstance(cluster, ve_cluster):
+        cluster = make_cluster(cluster)
+    h = c_void_p()
+    _check(_lib.ve_create(ctypes.byref(lattice), ctypes.byref(cluster), ctypes.byref(ham),
+                          ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)),
+           "ve_create")
+    return h.value
+
+
+def ve_iterate(h, max_iter, tol=0.0):
+    st = ve_status()
+    code = _check(_lib.ve_iterate(c_void_p(h), int(max_iter), float(tol), ctypes.byref(st)),
+                  "ve_iterate")
+    return code, st
+
+
+def ve_bound(h):
+    c = ve_cert()
+    _check(_lib.ve_bound(c_void_p(h), ctypes.byref(c)), "ve_bound")
+    return c
+
+
+def ve_destroy(h):
+    _lib.ve_destroy(c_void_p(h) if h else None)
+
+
+def ve_dims(h):
+    N, m, D = c_int(), c_int(), c_int()
+    _check(_lib.ve_dims(c_void_p(h), ctypes.byref(N), ctypes.byref(m), ctypes.byref(D)), "ve_dims")
+    return N.value, m.value, D.value
+
+
+def ve_state_size(h):
+    return _lib.ve_state_size(c_void_p(h))
+
+
+def ve_get_state(h, out=None):
+    n = ve_state_size(h)
+    if out is None:
+        out = np.empty(n // 8, dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.ve_get_state(c_void_p(h), out.ctypes.data_as(P_double), out.nbytes), "ve_get_state")
+    return out
+
+
+def ve_set_state(h, vec):
+    vec = np.ascontiguousarray(vec, dtype=np.float64)
+    _check(_lib.ve_set_state(c_void_p(h), vec.ctypes.data_as(P_double), vec.nbytes), "ve_set_state")
+
+
+def ve_get_status(h):
+    st = ve_status()
+    _check(_lib.ve_get_status(c_void_p(h), ctypes.byref(st)), "ve_get_status")
+    return st
+
+
+def ve_profile(h, enable):
+    _check(_lib.ve_profile(c_void_p(h), int(enable)), "ve_profile")
+
+
+def ve_profile_read(h):
+    ms = (c_double * VE_NSTAGE)()
+    n = (c_long * VE_NSTAGE)()
+    _check(_lib.ve_profile_read(c_void_p(h), ms, n), "ve_profile_read")
+    return {STAGES[i]: (ms[i], n[i]) for i in range(VE_NSTAGE)}
+
+
+def ve_project_psd_sym(in_ptr, out_ptr, n, count, precision=VE_PREC_FP64, stream=None):
+    return _check(_lib.ve_project_psd_sym(in_ptr, out_ptr, int(n), int(count), int(precision),
+                                          stream), "ve_project_psd_sym")
+
+
+def ve_project_psd_herm(in_ptr, out_ptr, n, count, precision=VE_PREC_FP64, stream=None):
+    return _check(_lib.ve_project_psd_herm(in_ptr, out_ptr, int(n), int(count), int(precision),
+                                           stream), "ve_project_psd_herm")
+
+
+def _M(M):
+    M = tuple(int(x) for x in M)
+    arr = (c_int * 2)(M[0], M[1] if len(M) > 1 else 1)
+    return len(M), arr
+
+
+def ve_circulant_workspace_size(M, D):
+    dim, arr = _M(M)
+    return _lib.ve_circulant_workspace_size(dim, arr, int(D))
+
+
+def ve_circulant_project(x_in_ptr, x_out_ptr, M, D, workspace_ptr, workspace_bytes,
+                         precision=VE_PREC_FP64, stream=None):
+    dim, arr = _M(M)
+    return _check(_lib.ve_circulant_project(x_in_ptr, x_out_ptr, dim, arr, int(D), int(precision),
+                                            workspace_ptr, int(workspace_bytes), stream),
+                  "ve_circulant_project")

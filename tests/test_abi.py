@@ -1,0 +1,123 @@
+"""The C-ABI library loads, exports every symbol include/ve.h declares, and its host-only entry
+points (no GPU work) behave as documented.  No kernel is launched here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle import models as mo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ve.h")
+
+
+@pytest.fixture(scope="module")
+def ve():
+    __graft_entry__.build()
+    from paper_2106_02682_gb300 import ve as mod
+    return mod
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ve_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(ve):
+    names = declared_functions()
+    assert len(names) >= 17
+    out = subprocess.run(["nm", "-D", "--defined-only", ve.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(ve_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(ve.lib, n)
+
+
+def test_struct_layouts_match_the_header(ve, tmp_path):
+    """Compile a C probe against include/ve.h and compare sizes/offsets with the ctypes mirror."""
+    structs = {"ve_lattice": ve.ve_lattice, "ve_cluster": ve.ve_cluster,
+               "ve_hamiltonian": ve.ve_hamiltonian, "ve_options": ve.ve_options,
+               "ve_status": ve.ve_status, "ve_cert": ve.ve_cert}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ve.h"', 'int main(void){']
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.splitlines():
+        name, field, val = line.split()
+        cls = structs[name]
+        if field == "size":
+            assert ctypes.sizeof(cls) == int(val), name
+        else:
+            assert getattr(cls, field).offset == int(val), (name, field)
+
+
+def test_defaults_and_error_strings(ve):
+    opt = ve.ve_default_options()
+    assert (opt.mu, opt.nu, opt.eps, opt.precision, opt.check_every) == (10.0, 10.0, 2.0, 0, 10)
+    assert opt.stream is None
+    for code in (0, 1, -1, -2, -3, -4, -5):
+        assert ve.ve_error_string(code) and ve.ve_error_string(code) != "unknown status"
+    assert ve.ve_error_string(42) == "unknown status"
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_site_terms_match_the_oracle_models(ve, dim):
+    for J, h in [(1.0, 0.5), (0.7, 1.3)]:
+        H = ve.ve_ham_tfim(dim, J, h)
+        on, bonds = mo.tfim_terms(J, h, dim)
+        np.testing.assert_array_equal(np.array(H.onsite).reshape(2, 2), on)
+        assert H.nbond == dim
+        for b, (off, B) in enumerate(bonds):
+            np.testing.assert_array_equal(np.array(H.bond[b]).reshape(4, 4), B)
+            assert tuple(H.bond_offset[b])[:dim] == off
+    for J, d in [(1.0, 1.0), (0.5, 0.3)]:
+        H = ve.ve_ham_xxz(dim, J, d)
+        on, bonds = mo.xxz_terms(J, d, dim)
+        np.testing.assert_allclose(np.array(H.bond[0]).reshape(4, 4), bonds[0][1], atol=1e-15)
+    with pytest.raises(ve.VEError):
+        ve.ve_ham_tfim(3, 1.0, 1.0)
+
+
+@pytest.mark.parametrize("lattice,cluster,code", [
+    ((8,), (3,), -1),          # cluster does not tile the lattice
+    ((2,), (2,), -1),          # a single cluster (N < 2)
+    ((16,), (4,), -5),         # 4-spin clusters: not built here
+    ((4 * 67,), (1,), -5),     # N = 268 > 64 does not split into two factors <= 64
+    ((8000,), (1,), -5),       # N > 4096
+    ((130, 4), (1, 1), -5),    # 2-D axis with more than 64 clusters
+])
+def test_create_rejects_bad_shapes_before_touching_the_gpu(ve, lattice, cluster, code):
+    with pytest.raises(ve.VEError) as ei:
+        ve.ve_create(lattice, cluster, ve.ve_ham_tfim(len(lattice), 1.0, 1.0))
+    assert ei.value.code == code
+
+
+def test_create_rejects_bad_options(ve):
+    for bad in (dict(mu=0.0), dict(nu=-1.0), dict(eps=0.0), dict(check_every=0), dict(precision=7)):
+        with pytest.raises(ve.VEError) as ei:
+            ve.ve_create((8,), (1,), ve.ve_ham_tfim(1, 1.0, 1.0), ve.ve_default_options(**bad))
+        assert ei.value.code == -1
+
+
+def test_null_handles_are_rejected(ve):
+    assert ve.lib.ve_iterate(None, 1, 0.0, None) == -1
+    assert ve.lib.ve_bound(None, None) == -1
+    assert ve.lib.ve_state_size(None) == 0
+    ve.ve_destroy(None)
+    assert ve.ve_circulant_workspace_size((3, 5), 16) > 0
+    assert ve.ve_circulant_workspace_size((4 * 67,), 16) == 0

@@ -1,0 +1,266 @@
+"""GPU parity: every step of the sweep through the C ABI against the CPU oracle, element by
+element, on the same seeded inputs.
+
+Tolerances (float64 mode): 1e-10 relative to the largest entry of the compared array, the
+target for float64 results; both sides run the same float64 arithmetic in a different order
+(Jacobi vs LAPACK eigensolver, FFT vs numpy FFT), so agreement is ~1e-13 in practice.  Float32
+projections (VE_PREC_MIXED) are held to 2e-5 relative, a bound on a float32 eigensolve of a
+<= 64 x 64 matrix (~n * 2^-24 * ||A||), and the final certified bound to 1e-6 per spin.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle import models as mo
+from oracle import ve_oracle as vo
+from paper_2106_02682_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+RTOL64 = 1e-10
+RTOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ve():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    __graft_entry__.build()
+    from paper_2106_02682_gb300 import ve as mod
+    return mod
+
+
+def relerr(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ------------------------------------------------------------------ S3: pair projections
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 64])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_project_sym_matches_oracle(ve, n, prec):
+    A = synth.symmetric_batch(1001 if n <= 16 else 131, n, seed=n)
+    x = dev(A)
+    y = torch.empty_like(x)
+    ve.ve_project_psd_sym(x.data_ptr(), y.data_ptr(), n, A.shape[0], prec)
+    torch.cuda.synchronize()
+    ref = vo.proj_psd(A)
+    out = y.cpu().numpy()
+    for b in range(A.shape[0]):
+        scale = max(1.0, np.max(np.abs(A[b])))
+        tol = RTOL64 if prec == 0 else RTOL32
+        assert np.max(np.abs(out[b] - ref[b])) <= tol * scale, b
+    # in place, and an empty batch
+    ve.ve_project_psd_sym(x.data_ptr(), x.data_ptr(), n, A.shape[0], prec)
+    ve.ve_project_psd_sym(x.data_ptr(), x.data_ptr(), n, 0, prec)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.cpu().numpy(), out)
+
+
+@pytest.mark.parametrize("n", [4, 16, 64])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_project_herm_matches_oracle(ve, n, prec):
+    A = synth.hermitian_batch(517 if n <= 16 else 67, n, seed=100 + n)
+    inter = np.stack([A.real, A.imag], axis=-1)
+    x = dev(inter)
+    y = torch.empty_like(x)
+    ve.ve_project_psd_herm(x.data_ptr(), y.data_ptr(), n, A.shape[0], prec)
+    torch.cuda.synchronize()
+    o = y.cpu().numpy()
+    out = o[..., 0] + 1j * o[..., 1]
+    ref = vo.proj_psd(A)
+    tol = RTOL64 if prec == 0 else RTOL32
+    for b in range(A.shape[0]):
+        assert np.max(np.abs(out[b] - ref[b])) <= tol * max(1.0, np.max(np.abs(A[b]))), b
+
+
+def test_projection_degenerate_cases(ve):
+    n = 16
+    cases = [np.zeros((n, n)), np.eye(n), -np.eye(n), np.diag(np.r_[np.ones(8), -np.ones(8)]),
+             np.ones((n, n)), -np.ones((n, n)), 1e-300 * np.eye(n), 1e12 * synth.symmetric_batch(1, n, 5)[0]]
+    A = np.array(cases)
+    x = dev(A)
+    y = torch.empty_like(x)
+    ve.ve_project_psd_sym(x.data_ptr(), y.data_ptr(), n, len(cases), 0)
+    torch.cuda.synchronize()
+    out = y.cpu().numpy()
+    ref = vo.proj_psd(A)
+    for b in range(len(cases)):
+        assert np.max(np.abs(out[b] - ref[b])) <= RTOL64 * max(1.0, np.max(np.abs(A[b]))), b
+
+
+# ------------------------------------------------------------------ S7-S9: the X step
+
+CIRC = [((2,), 4), ((3,), 16), ((5,), 4), ((16,), 16), ((64,), 16), ((100,), 4), ((96,), 16),
+        ((2048,), 16), ((4096,), 4), ((2, 3), 16), ((4, 4), 4), ((8, 6), 16), ((32, 32), 16),
+        ((3,), 64), ((2, 2), 64)]
+
+
+@pytest.mark.parametrize("M,D", CIRC)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_circulant_projection_matches_oracle(ve, M, D, prec):
+    if prec == 1 and D == 4 and np.prod(M) > 1000:
+        pytest.skip("covered by the float64 case")
+    X = synth.circulant_first_row(M, D, seed=int(np.prod(M)) + D)
+    ref = np.real(vo._lattice_dft(vo.proj_psd(vo._lattice_dft(X, M, False)), M, True))
+    ws_bytes = ve.ve_circulant_workspace_size(M, D)
+    ws = torch.empty(ws_bytes // 8 + 64, dtype=torch.float64, device="cuda")
+    x = dev(X)
+    y = torch.empty_like(x)
+    ve.ve_circulant_project(x.data_ptr(), y.data_ptr(), M, D, ws.data_ptr(), ws_bytes, prec)
+    torch.cuda.synchronize()
+    err = relerr(y.cpu().numpy(), ref)
+    assert err <= (RTOL64 if prec == 0 else 10 * RTOL32), err
+    # in place
+    ve.ve_circulant_project(x.data_ptr(), x.data_ptr(), M, D, ws.data_ptr(), ws_bytes, prec)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+def test_circulant_projection_rejects_small_workspace(ve):
+    M, D = (16,), 16
+    ws_bytes = ve.ve_circulant_workspace_size(M, D)
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device="cuda")
+    x = torch.zeros(16 * D * D, dtype=torch.float64, device="cuda")
+    with pytest.raises(ve.VEError):
+        ve.ve_circulant_project(x.data_ptr(), x.data_ptr(), M, D, ws.data_ptr(), ws_bytes - 256, 0)
+
+
+# ------------------------------------------------------------------ whole sweeps
+
+SWEEP_CASES = [
+    ((16,), (1,), "tfim", 1.0),
+    ((8,), (2,), "tfim", 0.7),
+    ((3,), (1,), "xxz", 0.4),
+    ((100,), (1,), "tfim", 0.5),
+    ((192,), (2,), "tfim", 1.2),
+    ((4, 4), (1, 1), "tfim", 2.0),
+    ((4, 6), (2, 1), "xxz", 0.5),
+    ((6, 4), (1, 2), "tfim", 3.0),
+    ((12,), (3,), "tfim", 1.0),
+    ((6, 4), (3, 1), "xxz", 1.0),
+]
+
+
+def _terms(kind, dim, x):
+    return mo.tfim_terms(1.0, x, dim) if kind == "tfim" else mo.xxz_terms(1.0, x, dim)
+
+
+def _ham(ve, kind, dim, x):
+    return ve.ve_ham_tfim(dim, 1.0, x) if kind == "tfim" else ve.ve_ham_xxz(dim, 1.0, x)
+
+
+@pytest.mark.parametrize("lattice,cluster,kind,x", SWEEP_CASES)
+def test_sweeps_match_oracle(ve, lattice, cluster, kind, x):
+    dim = len(lattice)
+    pb = vo.Problem(mo.cluster_model(lattice, cluster, *_terms(kind, dim, x)))
+    st = vo.initial_state(pb)
+    h = ve.ve_create(lattice, cluster, _ham(ve, kind, dim, x))
+    try:
+        assert ve.ve_dims(h) == (pb.N, pb.m, pb.D)
+        np.testing.assert_array_equal(ve.ve_get_state(h), vo.pack_state(pb, st))
+        done = 0
+        for k in (1, 6, 23):
+            code, status = ve.ve_iterate(h, k, 0.0)
+            for _ in range(k):
+                diag = vo.iterate(pb, st)
+            done += k
+            assert code == 0 and status.iter == done
+            err = relerr(ve.ve_get_state(h), vo.pack_state(pb, st))
+            assert err < RTOL64, (done, err)
+            assert abs(status.energy_per_spin - diag['energy']) < RTOL64
+            assert abs(status.feas_err - diag['feas_err']) < RTOL64 * max(1.0, diag['feas_err'])
+            if done > 1:
+                assert abs(status.d_energy - diag['d_energy']) < RTOL64
+        cert = ve.ve_bound(h)
+        ocert = vo.certified_bound(pb, st)
+        for key in ('bound_per_spin', 'raw_bound', 'x_neg_correction', 'primal_per_spin'):
+            assert abs(getattr(cert, key) - ocert[key]) <= RTOL64 * max(1.0, abs(ocert[key])), key
+        assert abs(cert.x_min_eig - ocert['x_min_eig']) < 1e-9
+    finally:
+        ve.ve_destroy(h)
+
+
+def test_full_size_workload_matches_oracle(ve):
+    """The benchmark workload (1-D TFI, h = 1, 2-spin clusters, 4096 clusters = 4096
+    wavevectors, D = 16), three sweeps, compared over the whole state."""
+    lattice, cluster = (8192,), (2,)
+    pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 1.0, 1)))
+    st = vo.initial_state(pb)
+    h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 1.0))
+    try:
+        _, status = ve.ve_iterate(h, 3, 0.0)
+        for _ in range(3):
+            diag = vo.iterate(pb, st)
+        assert relerr(ve.ve_get_state(h), vo.pack_state(pb, st)) < RTOL64
+        assert abs(status.energy_per_spin - diag['energy']) < RTOL64
+        cert = ve.ve_bound(h)
+        assert abs(cert.bound_per_spin - vo.certified_bound(pb, st)['bound_per_spin']) < RTOL64
+    finally:
+        ve.ve_destroy(h)
+
+
+def test_state_roundtrip_resume_and_determinism(ve):
+    lattice, cluster = (64,), (2,)
+    ham = ve.ve_ham_tfim(1, 1.0, 0.9)
+    a, b = ve.ve_create(lattice, cluster, ham), ve.ve_create(lattice, cluster, ham)
+    try:
+        ve.ve_iterate(a, 40, 0.0)
+        ve.ve_iterate(b, 25, 0.0)
+        snap = ve.ve_get_state(b)
+        ve.ve_set_state(b, snap)
+        ve.ve_iterate(b, 15, 0.0)
+        np.testing.assert_array_equal(ve.ve_get_state(a), ve.ve_get_state(b))
+        with pytest.raises(ve.VEError):
+            ve.ve_set_state(b, snap[:-1])
+        st = ve.ve_get_status(b)
+        assert st.iter == 40
+    finally:
+        ve.ve_destroy(a)
+        ve.ve_destroy(b)
+
+
+def test_nonfinite_state_is_reported(ve):
+    h = ve.ve_create((16,), (1,), ve.ve_ham_tfim(1, 1.0, 1.0))
+    try:
+        s = ve.ve_get_state(h)
+        s[0] = np.nan
+        ve.ve_set_state(h, s)
+        code = ve.lib.ve_iterate(ve.c_void_p(h), 10, 0.0, None)
+        assert code == ve.VE_ENONFINITE
+    finally:
+        ve.ve_destroy(h)
+
+
+def test_converges_to_the_paper_table_value(ve):
+    """TFI 20x1, 2x1 clusters, h = 1 (Sec. 4 table): 10 000 sweeps on the GPU."""
+    h = ve.ve_create((20,), (2,), ve.ve_ham_tfim(1, 1.0, 1.0))
+    try:
+        _, st = ve.ve_iterate(h, 10000, 0.0)
+        cert = ve.ve_bound(h)
+        assert abs(st.energy_per_spin - (-1.283534)) < 5e-6
+        assert -1.283534 - 5e-6 < cert.bound_per_spin <= -1.283534 + 1e-7
+    finally:
+        ve.ve_destroy(h)
+
+
+def test_mixed_precision_reaches_the_float64_bound(ve):
+    lattice, cluster = (32,), (2,)
+    ham = ve.ve_ham_tfim(1, 1.0, 1.0)
+    out = {}
+    for prec in (0, 1):
+        h = ve.ve_create(lattice, cluster, ham, ve.ve_default_options(precision=prec))
+        try:
+            code, st = ve.ve_iterate(h, 40000, 1e-6)
+            assert code == 0, st.as_dict()
+            out[prec] = ve.ve_bound(h).bound_per_spin
+        finally:
+            ve.ve_destroy(h)
+    assert abs(out[0] - out[1]) < 1e-6
+    assert out[1] <= mo.tfim_chain_jw_energy(32, 1.0, 1.0) / 32
