@@ -4,8 +4,9 @@ element, on the same seeded inputs.
 Tolerances (float64 mode): 1e-10 relative to the largest entry of the compared array, the
 target for float64 results; both sides run the same float64 arithmetic in a different order
 (Jacobi vs LAPACK eigensolver, FFT vs numpy FFT), so agreement is ~1e-13 in practice.  Float32
-projections (VE_PREC_MIXED) are held to 2e-5 relative, a bound on a float32 eigensolve of a
-<= 64 x 64 matrix (~n * 2^-24 * ||A||), and the final certified bound to 1e-6 per spin.
+projections (VE_PREC_MIXED) are held to 4 n 2^-24 ||A||_2 per entry, the backward-error bound of
+a float32 Jacobi eigensolve of an n x n matrix with a 4x margin, and the final certified bound
+to 1e-6 per spin.
 """
 import numpy as np
 import pytest
@@ -19,7 +20,12 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 RTOL64 = 1e-10
-RTOL32 = 2e-5
+RTOL32 = 2e-5    # relative tolerance of float32 results on O(1) arrays (X step, 16 x 16 blocks)
+
+
+def tol32(A):
+    """Per-entry tolerance of a float32 projection of the n x n matrix A."""
+    return 4.0 * A.shape[-1] * 2.0 ** -24 * np.linalg.norm(A, 2)
 
 
 @pytest.fixture(scope="module")
@@ -53,9 +59,8 @@ def test_project_sym_matches_oracle(ve, n, prec):
     ref = vo.proj_psd(A)
     out = y.cpu().numpy()
     for b in range(A.shape[0]):
-        scale = max(1.0, np.max(np.abs(A[b])))
-        tol = RTOL64 if prec == 0 else RTOL32
-        assert np.max(np.abs(out[b] - ref[b])) <= tol * scale, b
+        tol = RTOL64 * max(1.0, np.max(np.abs(A[b]))) if prec == 0 else tol32(A[b])
+        assert np.max(np.abs(out[b] - ref[b])) <= tol, b
     # in place, and an empty batch
     ve.ve_project_psd_sym(x.data_ptr(), x.data_ptr(), n, A.shape[0], prec)
     ve.ve_project_psd_sym(x.data_ptr(), x.data_ptr(), n, 0, prec)
@@ -75,9 +80,9 @@ def test_project_herm_matches_oracle(ve, n, prec):
     o = y.cpu().numpy()
     out = o[..., 0] + 1j * o[..., 1]
     ref = vo.proj_psd(A)
-    tol = RTOL64 if prec == 0 else RTOL32
     for b in range(A.shape[0]):
-        assert np.max(np.abs(out[b] - ref[b])) <= tol * max(1.0, np.max(np.abs(A[b]))), b
+        tol = RTOL64 * max(1.0, np.max(np.abs(A[b]))) if prec == 0 else tol32(A[b])
+        assert np.max(np.abs(out[b] - ref[b])) <= tol, b
 
 
 def test_projection_degenerate_cases(ve):
