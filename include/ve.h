@@ -187,6 +187,31 @@ size_t ve_circulant_workspace_size(int dim, const int M[2], int D);
 int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M[2], int D,
                          int precision, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- X step without allocation ----------------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that may not allocate
+ * device memory themselves: a plugin whose host framework owns every device allocation and
+ * hands it only input and output buffers, or a latency-critical loop in which cudaMalloc's
+ * implicit synchronisation and unpredictable latency are not allowed.
+ *
+ * ve_circulant_project_noalloc computes exactly what ve_circulant_project computes (same
+ * arguments, same kernels) but takes its scratch from a fixed array of
+ * VE_NOALLOC_SCRATCH_BYTES bytes compiled into this library (a file-scope __device__ array;
+ * every GPU that loads the library holds it until the process exits).  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Limit: the call needs
+ * ve_circulant_workspace_size(dim, M, D) <= VE_NOALLOC_SCRATCH_BYTES, which admits every
+ * first block row with N * D * D <= 2^20 float64 entries (e.g. 4096 clusters with D = 16);
+ * larger requests return VE_EINVAL before any GPU work.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress
+ *     with that device current); make that first call before any stream capture.
+ *   - All calls on a device share the one array and leave their data in it.  Calls whose GPU
+ *     work overlaps (other streams, or other host threads, without ordering between them) race
+ *     on it and produce wrong results; order them on one stream or with events.
+ * Errors: VE_EINVAL (NULL pointers, bad sizes, request above the limit), VE_EUNSUPPORTED (as
+ * for ve_circulant_project, or a device ordinal above 63), VE_ECUDA. */
+#define VE_NOALLOC_SCRATCH_BYTES ((size_t)(16u << 20) + (size_t)(256u << 10))
+int ve_circulant_project_noalloc(const double* x_in, double* x_out, int dim, const int M[2], int D,
+                                 int precision, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

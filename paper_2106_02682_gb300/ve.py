@@ -25,6 +25,7 @@ VE_PREC_FP64 = 0
 VE_PREC_MIXED = 1
 VE_MAX_BONDS = 4
 VE_NSTAGE = 7
+VE_NOALLOC_SCRATCH_BYTES = (16 << 20) + (256 << 10)
 STAGES = ("pair", "rho0", "dual12", "status", "fft_forward", "xproj", "fft_inverse")
 
 c_int, c_long, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_long, ctypes.c_double,
@@ -102,6 +103,8 @@ def _load():
         "ve_circulant_workspace_size": (c_size_t, [c_int, ctypes.POINTER(c_int), c_int]),
         "ve_circulant_project": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(c_int), c_int,
                                          c_int, c_void_p, c_size_t, c_void_p]),
+        "ve_circulant_project_noalloc": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(c_int),
+                                                 c_int, c_int, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -261,3 +264,11 @@ def ve_circulant_project(x_in_ptr, x_out_ptr, M, D, workspace_ptr, workspace_byt
     return _check(_lib.ve_circulant_project(x_in_ptr, x_out_ptr, dim, arr, int(D), int(precision),
                                             workspace_ptr, int(workspace_bytes), stream),
                   "ve_circulant_project")
+
+
+def ve_circulant_project_noalloc(x_in_ptr, x_out_ptr, M, D, precision=VE_PREC_FP64, stream=None):
+    """The X step with the library's fixed scratch array (no allocation; see include/ve.h)."""
+    dim, arr = _M(M)
+    return _check(_lib.ve_circulant_project_noalloc(x_in_ptr, x_out_ptr, dim, arr, int(D),
+                                                    int(precision), stream),
+                  "ve_circulant_project_noalloc")
