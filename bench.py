@@ -40,7 +40,10 @@ def parse():
     ap.add_argument("--workload", default="tfim1d_L2_N4096")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-ttb", action="store_true", help="skip the time-to-certified-bound runs")
-    ap.add_argument("--ttb-max-iter", type=int, default=60000)
+    ap.add_argument("--ttb-workload", default="tfim1d_L2_N50",
+                    help="instance of the time-to-certified-bound runs (default: the paper's TFI "
+                         "100x1 table instance, 2x1 clusters, h = 1)")
+    ap.add_argument("--ttb-max-iter", type=int, default=40000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -275,7 +278,6 @@ def run_ours(args):
                       "read-back, ve_get_state to pinned host; wall clock"}
 
         # ---- roofline of the dominant kernel, from the live per-stage events
-        ncanon = sum(1 for _ in range(1))  # replaced below
         ncanon = (N // 2 + 1) if dim == 1 else None
         if ncanon is None:
             M0 = w["lattice"][0] // w["cluster"][0]
@@ -317,9 +319,13 @@ def run_ours(args):
         # ---- time to certified bound, float64 and mixed, fresh handles
         ttb = None
         if not args.no_ttb and rank == 0:
-            ttb = {}
+            tw_ = synth.WORKLOADS[args.ttb_workload]
+            tdim = len(tw_["lattice"])
+            tham = (ve.ve_ham_tfim(tdim, 1.0, tw_["h"]) if tw_["kind"] == "tfim"
+                    else ve.ve_ham_xxz(tdim, 1.0, tw_["h"]))
+            ttb = {"workload": args.ttb_workload, "tol": 1e-6}
             for pname, pcode in (("fp64", ve.VE_PREC_FP64), ("mixed", ve.VE_PREC_MIXED)):
-                hh = ve.ve_create(w["lattice"], w["cluster"], ham,
+                hh = ve.ve_create(tw_["lattice"], tw_["cluster"], tham,
                                   ve.ve_default_options(precision=pcode, stream=stream.cuda_stream))
                 try:
                     torch.cuda.synchronize()

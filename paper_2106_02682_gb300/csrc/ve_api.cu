@@ -148,13 +148,17 @@ struct ve_handle {
          *lam2 = nullptr, *X = nullptr;
   double *a1r = nullptr, *a2r = nullptr, *part = nullptr, *part2 = nullptr, *hb = nullptr,
          *H0 = nullptr, *lmin_pairs = nullptr, *lmin_k = nullptr, *lmin0 = nullptr;
-  int *hslot = nullptr, *neg = nullptr;
+  int *hslot = nullptr, *neg = nullptr, *canon = nullptr;
+  int ncanon = 0;
   double2 *specA = nullptr, *specB = nullptr, *tw = nullptr;
+  // eigenvectors of the last projections, per precision (index 0: float64, 1: float32)
+  void* vpair[2] = {nullptr, nullptr};
+  void* vk[2] = {nullptr, nullptr};
+  bool vvalid[2] = {false, false};
   DevStatus* dst = nullptr;
   DevStatus* hst = nullptr;  // pinned
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaGraph_t graph[2] = {nullptr, nullptr};
-  bool warmed[2] = {false, false};
   bool fp64_phase = false;  // MIXED: switched to float64
   // per-stage profiling
   bool prof = false;
@@ -192,6 +196,8 @@ PairArgs pair_args(ve_handle* h) {
   a.a1r = h->a1r;
   a.a2r = h->a2r;
   a.part = h->part;
+  a.vstore = nullptr;
+  a.warm = 0;
   return a;
 }
 
@@ -219,9 +225,12 @@ SmallArgs small_args(ve_handle* h) {
 }
 
 // One sweep of Algorithm 6, all on h->stream (with stage events when profiling).
-cudaError_t issue_sweep(ve_handle* h, bool fp32) {
+cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
   cudaStream_t s = h->stream;
-  const PairArgs pa = pair_args(h);
+  const int v = fp32 ? 1 : 0;
+  PairArgs pa = pair_args(h);
+  pa.vstore = h->vpair[v];
+  pa.warm = warm ? 1 : 0;
   const SmallArgs sa = small_args(h);
   cudaError_t e;
   auto mark = [&](int i) { return h->prof ? cudaEventRecord(h->ev[i], s) : cudaSuccess; };
@@ -237,7 +246,8 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32) {
   double2* spec = nullptr;
   if ((e = fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, s)) != cudaSuccess) return e;
   if ((e = mark(5)) != cudaSuccess) return e;
-  if ((e = launch_xproj(h->plan, spec, fp32, s)) != cudaSuccess) return e;
+  if ((e = launch_xproj(h->plan, spec, h->canon, fp32, h->vk[v], warm ? 1 : 0, s)) != cudaSuccess)
+    return e;
   if ((e = mark(6)) != cudaSuccess) return e;
   if ((e = fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, s)) != cudaSuccess) return e;
   return mark(7);
@@ -254,8 +264,10 @@ int accumulate_profile(ve_handle* h) {
   return VE_OK;
 }
 
-// Run `count` sweeps: the first one of each precision directly (kernel attributes are set
-// outside any capture), the rest by replaying a captured one-sweep graph.
+// Run `count` sweeps.  The first sweep of a precision after ve_create / ve_set_state runs
+// directly and cold (Jacobi from V = I; it also sets kernel attributes outside any capture);
+// the others replay a captured one-sweep graph that starts every Jacobi from the eigenvectors
+// stored by the previous sweep.
 int read_status(ve_handle* h, ve_status* out);
 
 int run_sweeps(ve_handle* h, long count, bool fp32) {
@@ -263,23 +275,23 @@ int run_sweeps(ve_handle* h, long count, bool fp32) {
   if (count <= 0) return VE_OK;
   if (h->prof) {
     for (long i = 0; i < count; ++i) {
-      VE_CU(issue_sweep(h, fp32));
+      VE_CU(issue_sweep(h, fp32, h->vvalid[v]));
+      h->vvalid[v] = true;
       VE_CU(cudaStreamSynchronize(h->stream));
       const int r = accumulate_profile(h);
       if (r != VE_OK) return r;
     }
-    h->warmed[v] = true;
     return VE_OK;
   }
-  if (!h->warmed[v]) {
-    VE_CU(issue_sweep(h, fp32));
-    h->warmed[v] = true;
+  if (!h->vvalid[v]) {
+    VE_CU(issue_sweep(h, fp32, false));
+    h->vvalid[v] = true;
     --count;
   }
   if (count <= 0) return VE_OK;
   if (!h->exec[v]) {
     VE_CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = issue_sweep(h, fp32);
+    cudaError_t e = issue_sweep(h, fp32, true);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -435,6 +447,11 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   const size_t o_l0 = take(sizeof(double));
   const size_t o_hslot = take(sizeof(int) * N);
   const size_t o_neg = take(sizeof(int) * N);
+  const size_t o_canon = take(sizeof(int) * N);
+  const size_t o_vp64 = take(sizeof(double) * P * DD);
+  const size_t o_vp32 = take(sizeof(float) * P * DD);
+  const size_t o_vk64 = take(sizeof(double) * 2 * N * DD);
+  const size_t o_vk32 = take(sizeof(float) * 2 * N * DD);
   const size_t o_sa = take(sizeof(double2) * N * h->plan.E);
   const size_t o_sb = take(sizeof(double2) * N * h->plan.E);
   const size_t o_tw = take(sizeof(double2) * h->plan.ntw);
@@ -469,6 +486,12 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   h->lmin0 = (double*)(base + o_l0);
   h->hslot = (int*)(base + o_hslot);
   h->neg = (int*)(base + o_neg);
+  h->canon = (int*)(base + o_canon);
+  h->ncanon = fft_ncanon(h->plan);
+  h->vpair[0] = base + o_vp64;
+  h->vpair[1] = base + o_vp32;
+  h->vk[0] = base + o_vk64;
+  h->vk[1] = base + o_vk32;
   h->specA = (double2*)(base + o_sa);
   h->specB = (double2*)(base + o_sb);
   h->tw = (double2*)(base + o_tw);
@@ -512,6 +535,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->neg, md.neg.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->dst, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_fft_tables(h->plan, h->tw, h->stream);
+  if (e == cudaSuccess) e = launch_canon_list(h->plan, h->canon, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     ve_destroy(h);
@@ -571,6 +595,7 @@ int ve_set_state(ve_handle* h, const double* host, size_t bytes) {
   VE_CU(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
   VE_CU(cudaStreamSynchronize(h->stream));
   h->fp64_phase = false;
+  h->vvalid[0] = h->vvalid[1] = false;
   return VE_OK;
 }
 
@@ -632,14 +657,15 @@ int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out) {
     }
     if (tol > 0) {
       if (fp32) {
-        // float32 projections until the residual is within 10x of the target or stops falling
+        // float32 projections until the residual meets the target or has not fallen by 1 %
+        // over 100 read-backs (the float32 rounding floor); float64 sweeps then finish the solve
         if (s.residual < 0.99 * best) {
           best = s.residual;
           stall = 0;
         } else {
           ++stall;
         }
-        if (s.residual <= 10.0 * tol || stall >= 20) h->fp64_phase = true;
+        if (s.residual <= tol || stall >= 100) h->fp64_phase = true;
       } else if (s.residual <= tol) {
         rc = VE_OK;
         break;
@@ -658,7 +684,7 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   const int N = md.N, P = h->P;
   double2* spec = nullptr;
   VE_CU(fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, h->stream));
-  VE_CU(launch_xeig(h->plan, spec, h->lmin_k, h->stream));
+  VE_CU(launch_xeig(h->plan, spec, h->canon, h->lmin_k, h->stream));
   BoundArgs b;
   b.N = N;
   b.P = P;
@@ -673,10 +699,11 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   b.lmin_pairs = h->lmin_pairs;
   b.lmin0 = h->lmin0;
   VE_CU(launch_bound(b, h->stream));
-  std::vector<double> lp(P), lk(N);
+  std::vector<double> lp(P), lk(h->ncanon);
   double l0 = 0;
   VE_CU(cudaMemcpyAsync(lp.data(), h->lmin_pairs, sizeof(double) * P, cudaMemcpyDeviceToHost, h->stream));
-  VE_CU(cudaMemcpyAsync(lk.data(), h->lmin_k, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  VE_CU(cudaMemcpyAsync(lk.data(), h->lmin_k, sizeof(double) * h->ncanon, cudaMemcpyDeviceToHost,
+                        h->stream));
   VE_CU(cudaMemcpyAsync(&l0, h->lmin0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   ve_status s;
   int r = read_status(h, &s);  // synchronises the stream
@@ -684,7 +711,7 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   double raw = (double)N * l0;
   for (int p = 0; p < P; ++p) raw += (double)md.count[p + 1] * lp[p];
   double xmin = INFINITY;
-  for (int k = 0; k < N; ++k) xmin = lk[k] < xmin ? lk[k] : xmin;
+  for (int k = 0; k < h->ncanon; ++k) xmin = lk[k] < xmin ? lk[k] : xmin;
   const double corr = (double)N * md.m * (xmin < 0 ? -xmin : 0.0);
   const double spins = (double)N * md.L;
   out->raw_bound = raw;
@@ -717,7 +744,8 @@ size_t ve_circulant_workspace_size(int dim, const int M[2], int D) {
   if (!M) return 0;
   FftPlan p;
   if (fft_plan_build(p, dim, M, D) != 0) return 0;
-  return align_up(sizeof(double2) * (size_t)p.N * p.E) * 2 + align_up(sizeof(double2) * p.ntw);
+  return align_up(sizeof(double2) * (size_t)p.N * p.E) * 2 + align_up(sizeof(double2) * p.ntw) +
+         align_up(sizeof(int) * (size_t)p.N);
 }
 
 int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M[2], int D,
@@ -729,16 +757,19 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
   const int rc = fft_plan_build(p, dim, M, D);
   if (rc != 0) return rc;
   const size_t sb = align_up(sizeof(double2) * (size_t)p.N * p.E);
-  if (workspace_bytes < 2 * sb + align_up(sizeof(double2) * p.ntw)) return VE_EINVAL;
+  const size_t stw = align_up(sizeof(double2) * p.ntw);
+  if (workspace_bytes < 2 * sb + stw + align_up(sizeof(int) * (size_t)p.N)) return VE_EINVAL;
   char* w = (char*)workspace;
   double2* A = (double2*)w;
   double2* B = (double2*)(w + sb);
   double2* tw = (double2*)(w + 2 * sb);
+  int* canon = (int*)(w + 2 * sb + stw);
   cudaStream_t s = (cudaStream_t)stream;
   VE_CU(launch_fft_tables(p, tw, s));
+  VE_CU(launch_canon_list(p, canon, s));
   double2* spec = nullptr;
   VE_CU(fft_forward(p, x_in, A, B, tw, &spec, s));
-  VE_CU(launch_xproj(p, spec, precision == VE_PREC_MIXED, s));
+  VE_CU(launch_xproj(p, spec, canon, precision == VE_PREC_MIXED, nullptr, 0, s));
   VE_CU(fft_inverse(p, spec, A, B, x_out, tw, s));
   return VE_OK;
 }

@@ -93,29 +93,110 @@ struct JacobiTol<float> {
 };
 
 // Rotation (c, s) that annihilates the (p,q) entry of [[app, apq], [apq, aqq]] with
-// J = [[c, s], [-s, c]] (Golub & Van Loan, symmetric 2x2 Schur decomposition).
+// J = [[c, s], [-s, c]] (Golub & Van Loan, symmetric 2x2 Schur decomposition): the tangent t is
+// the root of smallest magnitude of b t^2 + d t - b = 0 (d = aqq - app, b = apq), i.e.
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = d / (2 b), and c = 1 / sqrt(1 + t^2), s = t c.
+//
+// float: evaluated directly.  double: the float64 divide and square root are long multi-
+// instruction sequences on a part with a narrow float64 pipe, so (d, b) are scaled by a power of
+// two into [1, 2), t is seeded in float32 and refined by two float64 Newton steps on the
+// quadratic (each squares the relative error: 1e-7 -> 1e-14 -> 1e-16; the derivative
+// 2 b t + d never falls below max(|d|, 2|b|) >= 1 near the root), and c by two Newton steps of
+// the reciprocal square root seeded in float32.  c^2 + s^2 = 1 to float64 rounding, which is
+// what keeps the accumulated eigenvectors orthogonal.
 template <typename T>
-__device__ __forceinline__ void sym_schur2(T app, T aqq, T apq, T& c, T& s) {
-  if (apq == T(0)) {
-    c = T(1);
-    s = T(0);
+__device__ __forceinline__ void sym_schur2(T app, T aqq, T apq, T& c, T& s);
+
+template <>
+__device__ __forceinline__ void sym_schur2<float>(float app, float aqq, float apq, float& c, float& s) {
+  if (apq == 0.f) {
+    c = 1.f;
+    s = 0.f;
     return;
   }
-  const T tau = (aqq - app) / (T(2) * apq);
-  const T at = fabs(tau);
-  T t;
-  if (at > JacobiTol<T>::big) {
-    t = T(0.5) / tau;
-  } else {
-    t = copysign(T(1), tau) / (at + sqrt(T(1) + tau * tau));
-  }
-  c = T(1) / sqrt(T(1) + t * t);
+  const float tau = (aqq - app) / (2.f * apq);
+  const float at = fabsf(tau);
+  const float t = (at > JacobiTol<float>::big) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
+  c = rsqrtf(1.f + t * t);
   s = t * c;
+}
+
+// 2^-e for the float64 exponent e of x (x finite, nonzero): scales x into [1, 2).  The
+// reciprocal 2^e is returned in *inv when requested.
+__device__ __forceinline__ double pow2_inverse_scale(double x, double* inv = nullptr) {
+  int ex = (__double2hiint(x) >> 20) & 0x7ff;
+  ex = ex < 1 ? 1 : (ex > 2045 ? 2045 : ex);
+  if (inv) *inv = __hiloint2double(ex << 20, 0);
+  return __hiloint2double((2046 - ex) << 20, 0);
+}
+
+template <>
+__device__ __forceinline__ void sym_schur2<double>(double app, double aqq, double apq, double& c,
+                                                   double& s) {
+  if (apq == 0.0) {
+    c = 1.0;
+    s = 0.0;
+    return;
+  }
+  const double d0 = aqq - app;
+  const double sc = pow2_inverse_scale(fmax(fabs(d0), fabs(apq)));
+  const double d = d0 * sc, b = apq * sc;  // exact; max(|d|, |b|) in [1, 2)
+  const float df = (float)d, bf = (float)b;
+  float tf = 0.f;
+  if (bf != 0.f) {
+    const float tau = df / (2.f * bf);
+    const float at = fabsf(tau);
+    tf = (at > 1e18f) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
+  }
+  double t = (double)tf;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double g = fma(fma(b, t, d), t, -b);
+    const double gp = fma(2.0 * b, t, d);
+    t = fma(-g, (double)__frcp_rn((float)gp), t);
+  }
+  const double u = fma(t, t, 1.0);  // in [1, 2]
+  const double hu = -0.5 * u;
+  double y = (double)rsqrtf((float)u);
+  y = y * fma(hu, y * y, 1.5);
+  y = y * fma(hu, y * y, 1.5);
+  c = y;
+  s = t * y;
+}
+
+// |b| and the unit phase w = conj(b) / |b| of b = (br, bi), b != 0, without a float64 divide or
+// square root (power-of-two scaling, float32 seed, two float64 Newton steps of rsqrt).
+template <typename T>
+__device__ __forceinline__ void unit_phase(T br, T bi, T& mag, T& wr, T& wi);
+
+template <>
+__device__ __forceinline__ void unit_phase<float>(float br, float bi, float& mag, float& wr, float& wi) {
+  const float q = br * br + bi * bi;
+  const float r = rsqrtf(q);
+  mag = q * r;
+  wr = br * r;
+  wi = -bi * r;
+}
+
+template <>
+__device__ __forceinline__ void unit_phase<double>(double br, double bi, double& mag, double& wr,
+                                                   double& wi) {
+  double isc;
+  const double sc = pow2_inverse_scale(fmax(fabs(br), fabs(bi)), &isc);
+  const double xr = br * sc, xi = bi * sc;
+  const double q = fma(xr, xr, xi * xi);  // in [1, 8)
+  const double hq = -0.5 * q;
+  double y = (double)rsqrtf((float)q);
+  y = y * fma(hq, y * y, 1.5);
+  y = y * fma(hq, y * y, 1.5);
+  wr = xr * y;
+  wi = -xi * y;
+  mag = (q * y) * isc;  // times a power of two: exact
 }
 
 // Real symmetric Jacobi on A (n x n, leading dimension LD) in shared memory.  If VEC, V (same
 // layout) receives the eigenvectors.  cs: shared scratch of n entries; red: NT/32 entries.
-template <typename T, int n, int LD, int NT, bool VEC>
+template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
 __device__ void jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
   constexpr int H = n / 2;
   T nrm = T(0);
@@ -124,7 +205,7 @@ __device__ void jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
     nrm += a * a;
   }
   nrm = gsum<NT>(nrm, red);
-  if constexpr (VEC) {
+  if constexpr (VEC && INIT_V) {
     for (int e = tid; e < n * n; e += NT) V[(e / n) * LD + (e % n)] = (e / n == e % n) ? T(1) : T(0);
   }
   gsync<NT>();
@@ -188,7 +269,7 @@ __device__ void jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
 // Complex Hermitian Jacobi on (Ar, Ai).  For the pair (p, q) with a_pq = |b| e^{i phi} the
 // unitary U = diag(1, w) J, w = e^{-i phi}, J the real rotation of [[a_pp, |b|], [|b|, a_qq]],
 // diagonalises the 2x2 block; A <- U^H A U, V <- V U.  cs: shared scratch of 2n entries.
-template <typename T, int n, int LD, int NT, bool VEC>
+template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
 __device__ void jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
   constexpr int H = n / 2;
   T nrm = T(0);
@@ -197,7 +278,7 @@ __device__ void jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) 
     nrm += Ar[o] * Ar[o] + Ai[o] * Ai[o];
   }
   nrm = gsum<NT>(nrm, red);
-  if constexpr (VEC) {
+  if constexpr (VEC && INIT_V) {
     for (int e = tid; e < n * n; e += NT) {
       const int o = (e / n) * LD + (e % n);
       Vr[o] = (e / n == e % n) ? T(1) : T(0);
@@ -221,13 +302,9 @@ __device__ void jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) 
         int p, q;
         rr_pair(n, r, k, p, q);
         const T br = Ar[p * LD + q], bi = Ai[p * LD + q];
-        const T mag = hypot(br, bi);
-        T c, s, wr = T(1), wi = T(0);
+        T c, s, mag = T(0), wr = T(1), wi = T(0);
+        if (br != T(0) || bi != T(0)) unit_phase<T>(br, bi, mag, wr, wi);
         sym_schur2<T>(Ar[p * LD + p], Ar[q * LD + q], mag, c, s);
-        if (mag > T(0)) {
-          wr = br / mag;
-          wi = -bi / mag;
-        }
         cs[k] = c;
         cs[H + k] = s;
         cs[2 * H + k] = wr;

@@ -144,7 +144,7 @@ template <int D, typename T>
 struct XSmem {
   static constexpr int LD = GroupShape<D>::LD;
   static constexpr size_t MAT = ((sizeof(T) * D * LD + 15) / 16) * 16;
-  static constexpr size_t bytes = 4 * MAT + ((sizeof(T) * 2 * D + 15) / 16) * 16 +
+  static constexpr size_t bytes = 6 * MAT + ((sizeof(T) * 2 * D + 15) / 16) * 16 +
                                   ((sizeof(T) * D + 15) / 16) * 16 + 16 * sizeof(T);
 };
 
@@ -186,7 +186,8 @@ __device__ void unpack_block(const double2* spec, int s, int s2, int E, T* Ar, T
 
 template <int D, typename T>
 __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
-    k_xproj(double2* spec, const FftPlan p, const double invN) {
+    k_xproj(double2* spec, const int* __restrict__ canon, const int ncanon, const FftPlan p,
+            const double invN, T* vstore, const int warm) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
   constexpr int GPC = (NT == 32) ? 4 : 1;
   using S = XSmem<D, T>;
@@ -197,15 +198,65 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
   T* Ai = reinterpret_cast<T*>(base + S::MAT);
   T* Vr = reinterpret_cast<T*>(base + 2 * S::MAT);
   T* Vi = reinterpret_cast<T*>(base + 3 * S::MAT);
-  T* cs = reinterpret_cast<T*>(base + 4 * S::MAT);
+  T* Wr = reinterpret_cast<T*>(base + 4 * S::MAT);
+  T* Wi = reinterpret_cast<T*>(base + 5 * S::MAT);
+  T* cs = reinterpret_cast<T*>(base + 6 * S::MAT);
   T* W = cs + 2 * D;
   T* red = W + D;
   const int E = p.E;
-  for (int s = blockIdx.x * GPC + g; s < p.N; s += gridDim.x * GPC) {
+  for (int j = blockIdx.x * GPC + g; j < ncanon; j += gridDim.x * GPC) {
+    const int s = canon[j];
     const int s2 = partner_slot(p, s);
-    if (s2 < s) continue;
     unpack_block<D, NT, LD, T>(spec, s, s2, E, Ar, Ai, tid);
-    jacobi_herm<T, D, LD, NT, true>(Ar, Ai, Vr, Vi, cs, red, tid);
+    T* vr = vstore ? vstore + (long)s * 2 * D * D : nullptr;
+    T* vi = vr ? vr + D * D : nullptr;
+    if (warm && vr) {
+      // start from the previous eigenvectors: A <- V^H C V
+      for (int e = tid; e < D * D; e += NT) {
+        Vr[(e / D) * LD + (e % D)] = vr[e];
+        Vi[(e / D) * LD + (e % D)] = vi[e];
+      }
+      gsync<NT>();
+      for (int e = tid; e < D * D; e += NT) {  // W = C V
+        const int i = e / D, jj = e % D;
+        T xr = T(0), xi = T(0);
+        for (int k = 0; k < D; ++k) {
+          const T ar = Ar[i * LD + k], ai = Ai[i * LD + k];
+          const T br = Vr[k * LD + jj], bi = Vi[k * LD + jj];
+          xr += ar * br - ai * bi;
+          xi += ar * bi + ai * br;
+        }
+        Wr[i * LD + jj] = xr;
+        Wi[i * LD + jj] = xi;
+      }
+      gsync<NT>();
+      for (int e = tid; e < D * D; e += NT) {  // A = V^H W, Hermitian
+        const int i = e / D, jj = e % D;
+        if (i <= jj) {
+          T xr = T(0), xi = T(0);
+          for (int k = 0; k < D; ++k) {
+            const T ar = Vr[k * LD + i], ai = -Vi[k * LD + i];
+            const T br = Wr[k * LD + jj], bi = Wi[k * LD + jj];
+            xr += ar * br - ai * bi;
+            xi += ar * bi + ai * br;
+          }
+          Ar[i * LD + jj] = xr;
+          Ar[jj * LD + i] = xr;
+          Ai[i * LD + jj] = (i == jj) ? T(0) : xi;
+          Ai[jj * LD + i] = (i == jj) ? T(0) : -xi;
+        }
+      }
+      gsync<NT>();
+      jacobi_herm<T, D, LD, NT, true, false>(Ar, Ai, Vr, Vi, cs, red, tid);
+    } else {
+      jacobi_herm<T, D, LD, NT, true, true>(Ar, Ai, Vr, Vi, cs, red, tid);
+    }
+    if (vr) {
+      for (int e = tid; e < D * D; e += NT) {
+        vr[e] = Vr[(e / D) * LD + (e % D)];
+        vi[e] = Vi[(e / D) * LD + (e % D)];
+      }
+    }
     for (int k = tid; k < D; k += NT) {
       const T w = Ar[k * LD + k];
       W[k] = w > T(0) ? w : T(0);
@@ -213,20 +264,20 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
     gsync<NT>();
     // Y = V diag(max(w,0)) V^H, written back into (Ar, Ai)
     for (int f = tid; f < D * D; f += NT) {
-      const int i = f / D, j = f % D;
-      if (i <= j) {
+      const int i = f / D, jj = f % D;
+      if (i <= jj) {
         T yr = T(0), yi = T(0);
         for (int k = 0; k < D; ++k) {
           const T w = W[k];
           const T air = Vr[i * LD + k], aii = Vi[i * LD + k];
-          const T ajr = Vr[j * LD + k], aji = Vi[j * LD + k];
+          const T ajr = Vr[jj * LD + k], aji = Vi[jj * LD + k];
           yr += w * (air * ajr + aii * aji);
           yi += w * (aii * ajr - air * aji);
         }
-        Ar[i * LD + j] = yr;
-        Ai[i * LD + j] = yi;
-        Ar[j * LD + i] = yr;
-        Ai[j * LD + i] = -yi;
+        Ar[i * LD + jj] = yr;
+        Ai[i * LD + jj] = yi;
+        Ar[jj * LD + i] = yr;
+        Ai[jj * LD + i] = -yi;
       }
     }
     gsync<NT>();
@@ -244,9 +295,34 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
   }
 }
 
+// One CTA: canonical slots in increasing order (block-wide scan over chunks of 256 slots).
+__global__ void __launch_bounds__(256) k_canon_list(const FftPlan p, int* canon) {
+  __shared__ int scan[256];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < p.N; c0 += 256) {
+    const int s = c0 + threadIdx.x;
+    const int flag = (s < p.N && s <= partner_slot(p, s)) ? 1 : 0;
+    scan[threadIdx.x] = flag;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+      const int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+      __syncthreads();
+      scan[threadIdx.x] += v;
+      __syncthreads();
+    }
+    if (flag) canon[base + scan[threadIdx.x] - 1] = s;
+    __syncthreads();
+    if (threadIdx.x == 255) base += scan[255];
+    __syncthreads();
+  }
+}
+
 template <int D>
 __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
-    k_xeig(const double2* spec, const FftPlan p, double* lmin) {
+    k_xeig(const double2* spec, const int* __restrict__ canon, const int ncanon, const FftPlan p,
+           double* lmin) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
   constexpr int GPC = (NT == 32) ? 4 : 1;
   using S = XSmem<D, double>;
@@ -257,44 +333,50 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
   double* Ai = reinterpret_cast<double*>(base + S::MAT);
   double* cs = reinterpret_cast<double*>(base + 4 * S::MAT);
   double* red = cs + 3 * D;
-  for (int s = blockIdx.x * GPC + g; s < p.N; s += gridDim.x * GPC) {
+  for (int j = blockIdx.x * GPC + g; j < ncanon; j += gridDim.x * GPC) {
+    const int s = canon[j];
     const int s2 = partner_slot(p, s);
-    if (s2 < s) {
-      if (tid == 0) lmin[s] = INFINITY;
-      continue;
-    }
     unpack_block<D, NT, LD, double>(spec, s, s2, p.E, Ar, Ai, tid);
     jacobi_herm<double, D, LD, NT, false>(Ar, Ai, nullptr, nullptr, cs, red, tid);
     double w = INFINITY;
     for (int k = tid; k < D; k += NT) w = fmin(w, Ar[k * LD + k]);
     w = gmin<NT>(w, red);
-    if (tid == 0) lmin[s] = w;
+    if (tid == 0) lmin[j] = w;
     gsync<NT>();
   }
 }
 
 
 template <int D, typename T>
-cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, cudaStream_t s) {
+cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, void* vstore,
+                           int warm, cudaStream_t s) {
   constexpr int NT = GroupShape<D>::NT, GPC = (NT == 32) ? 4 : 1;
   const size_t smem = XSmem<D, T>::bytes * GPC;
   static unsigned long long mask = 0;
   cudaError_t e = smem_once(k_xproj<D, T>, smem, mask);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((p.N + GPC - 1) / GPC);
-  k_xproj<D, T><<<blocks, NT * GPC, smem, s>>>(spec, p, 1.0 / p.N);
+  const int nc = fft_ncanon(p);
+  long blocks = (nc + GPC - 1) / GPC;
+  const long res = resident_grid((const void*)k_xproj<D, T>, NT * GPC, smem);
+  if (blocks > res) blocks = res;
+  k_xproj<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(spec, canon, nc, p, 1.0 / p.N,
+                                                          reinterpret_cast<T*>(vstore), warm);
   return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_xeig_t(const FftPlan& p, const double2* spec, double* lmin, cudaStream_t s) {
+cudaError_t launch_xeig_t(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
+                          cudaStream_t s) {
   constexpr int NT = GroupShape<D>::NT, GPC = (NT == 32) ? 4 : 1;
   const size_t smem = XSmem<D, double>::bytes * GPC;
   static unsigned long long mask = 0;
   cudaError_t e = smem_once(k_xeig<D>, smem, mask);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((p.N + GPC - 1) / GPC);
-  k_xeig<D><<<blocks, NT * GPC, smem, s>>>(spec, p, lmin);
+  const int nc = fft_ncanon(p);
+  long blocks = (nc + GPC - 1) / GPC;
+  const long res = resident_grid((const void*)k_xeig<D>, NT * GPC, smem);
+  if (blocks > res) blocks = res;
+  k_xeig<D><<<(unsigned)blocks, NT * GPC, smem, s>>>(spec, canon, nc, p, lmin);
   return cudaGetLastError();
 }
 
@@ -422,22 +504,43 @@ cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2*
   return run_pass(p, p.inv[1], +1, nullptr, other, nullptr, x, tw, s);
 }
 
-cudaError_t launch_xproj(const FftPlan& p, double2* spec, bool fp32, cudaStream_t s) {
+cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
+                         void* vstore, int warm, cudaStream_t s) {
   switch (p.D) {
-    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, s) : launch_xproj_t<4, double>(p, spec, s);
-    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, s) : launch_xproj_t<16, double>(p, spec, s);
-    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, s) : launch_xproj_t<64, double>(p, spec, s);
+    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, canon, vstore, warm, s)
+                        : launch_xproj_t<4, double>(p, spec, canon, vstore, warm, s);
+    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, canon, vstore, warm, s)
+                         : launch_xproj_t<16, double>(p, spec, canon, vstore, warm, s);
+    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, canon, vstore, warm, s)
+                         : launch_xproj_t<64, double>(p, spec, canon, vstore, warm, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_xeig(const FftPlan& p, const double2* spec, double* lmin, cudaStream_t s) {
+cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
+                        cudaStream_t s) {
   switch (p.D) {
-    case 4: return launch_xeig_t<4>(p, spec, lmin, s);
-    case 16: return launch_xeig_t<16>(p, spec, lmin, s);
-    case 64: return launch_xeig_t<64>(p, spec, lmin, s);
+    case 4: return launch_xeig_t<4>(p, spec, canon, lmin, s);
+    case 16: return launch_xeig_t<16>(p, spec, canon, lmin, s);
+    case 64: return launch_xeig_t<64>(p, spec, canon, lmin, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_canon_list(const FftPlan& p, int* canon, cudaStream_t s) {
+  k_canon_list<<<1, 256, 0, s>>>(p, canon);
+  return cudaGetLastError();
+}
+
+int fft_ncanon(const FftPlan& p) {
+  // k and -k pair up; the self-conjugate wavevectors (2k = 0 on every axis) stand alone
+  int selfc = 1;
+  if (p.dim == 1) {
+    selfc = (p.N % 2 == 0) ? 2 : 1;
+  } else {
+    selfc = ((p.M0 % 2 == 0) ? 2 : 1) * ((p.M1 % 2 == 0) ? 2 : 1);
+  }
+  return (p.N - selfc) / 2 + selfc;
 }
 
 }  // namespace ve

@@ -36,6 +36,8 @@ struct PairArgs {
   double* a1r;          // P*m*m   A1[rho_{0,delta}]
   double* a2r;          // P*m*m   A2[rho_{0,delta}]
   double* part;         // P*2     ||rho - rho~||^2, Tr[H rho]
+  void* vstore;         // P*D*D eigenvectors of the last projection (float or double)
+  int warm;             // 1: start each Jacobi from V^T C V with the stored V
 };
 
 struct DevStatus {
@@ -60,6 +62,9 @@ struct SmallArgs {
   double* part2;  // P: ||A1 rho - rho0||^2 + ||A2 rho - rho0||^2
   DevStatus* st;
 };
+
+// Number of CTAs that keep every SM busy for a kernel with the given block shape.
+int resident_grid(const void* kernel, int threads, size_t smem);
 
 // D in {4, 16, 64}; fp32 selects the float32 projection.
 cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s);
@@ -96,10 +101,16 @@ cudaError_t fft_forward(const FftPlan& p, const double* x, double2* bufA, double
 // Inverse: spectrum (in `spec`, which is bufA or bufB) -> real first block row x.
 cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2* bufB, double* x,
                         const double2* tw, cudaStream_t s);
-// Per-wavevector projection in place on the spectrum, scaled by 1/N.
-cudaError_t launch_xproj(const FftPlan& p, double2* spec, bool fp32, cudaStream_t s);
+// List of the canonical spectrum slots (s <= slot of -k), ncanon of them, in increasing order.
+cudaError_t launch_canon_list(const FftPlan& p, int* canon, cudaStream_t s);
+int fft_ncanon(const FftPlan& p);
+// Per-wavevector projection in place on the spectrum, scaled by 1/N.  vstore (N * 2 * D*D of
+// float or double, or null): eigenvectors kept per slot; warm = 1 starts from them.
+cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
+                         void* vstore, int warm, cudaStream_t s);
 // lmin[slot] = smallest eigenvalue of the (unnormalised) block C_k, +inf for non-canonical slots.
-cudaError_t launch_xeig(const FftPlan& p, const double2* spec, double* lmin, cudaStream_t s);
+cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
+                       cudaStream_t s);
 
 // ------------------------------------------------------------------ bound
 struct BoundArgs {

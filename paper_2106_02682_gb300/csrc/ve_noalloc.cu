@@ -49,7 +49,8 @@ extern "C" int ve_circulant_project_noalloc(const double* x_in, double* x_out, i
   const int rc = fft_plan_build(p, dim, M, D);
   if (rc != 0) return rc;
   const size_t sb = align_up(sizeof(double2) * (size_t)p.N * p.E);
-  const size_t need = 2 * sb + align_up(sizeof(double2) * p.ntw);
+  const size_t stw = align_up(sizeof(double2) * p.ntw);
+  const size_t need = 2 * sb + stw + align_up(sizeof(int) * (size_t)p.N);
   if (need > VE_NOALLOC_SCRATCH_BYTES) return VE_EINVAL;
   void* scratch = nullptr;
   const int r = scratch_address(&scratch);
@@ -58,13 +59,16 @@ extern "C" int ve_circulant_project_noalloc(const double* x_in, double* x_out, i
   double2* A = (double2*)w;
   double2* B = (double2*)(w + sb);
   double2* tw = (double2*)(w + 2 * sb);
+  int* canon = (int*)(w + 2 * sb + stw);
   cudaStream_t s = (cudaStream_t)stream;
-  // nothing in the scratch has to start at zero: the tables and both spectra are fully
-  // rewritten by this call before they are read
+  // nothing in the scratch has to start at zero: the tables, the wavevector list and both
+  // spectra are fully rewritten by this call before they are read
   if (launch_fft_tables(p, tw, s) != cudaSuccess) return VE_ECUDA;
+  if (launch_canon_list(p, canon, s) != cudaSuccess) return VE_ECUDA;
   double2* spec = nullptr;
   if (fft_forward(p, x_in, A, B, tw, &spec, s) != cudaSuccess) return VE_ECUDA;
-  if (launch_xproj(p, spec, precision == VE_PREC_MIXED, s) != cudaSuccess) return VE_ECUDA;
+  if (launch_xproj(p, spec, canon, precision == VE_PREC_MIXED, nullptr, 0, s) != cudaSuccess)
+    return VE_ECUDA;
   if (fft_inverse(p, spec, A, B, x_out, tw, s) != cudaSuccess) return VE_ECUDA;
   return VE_OK;
 }

@@ -34,7 +34,8 @@ struct PairSmem {
   static constexpr size_t Xs = R + sizeof(double) * D * D;           // double D*D
   static constexpr size_t A = Xs + sizeof(double) * D * D;           // T D*LD
   static constexpr size_t V = A + ((sizeof(T) * D * LD + 15) / 16) * 16;
-  static constexpr size_t CS = V + ((sizeof(T) * D * LD + 15) / 16) * 16;  // T D
+  static constexpr size_t WT = V + ((sizeof(T) * D * LD + 15) / 16) * 16;  // T D*LD
+  static constexpr size_t CS = WT + ((sizeof(T) * D * LD + 15) / 16) * 16;  // T D
   static constexpr size_t W = CS + ((sizeof(T) * D + 15) / 16) * 16;       // T D
   static constexpr size_t TR = W + ((sizeof(T) * D + 15) / 16) * 16;       // double 2*m*m + 2
   static constexpr size_t RED = TR + ((sizeof(double) * (2 * m * m + 2) + 15) / 16) * 16;
@@ -55,6 +56,7 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
   double* Xs = reinterpret_cast<double*>(base + S::Xs);
   T* A = reinterpret_cast<T*>(base + S::A);
   T* V = reinterpret_cast<T*>(base + S::V);
+  T* Wt = reinterpret_cast<T*>(base + S::WT);
   T* cs = reinterpret_cast<T*>(base + S::CS);
   T* W = reinterpret_cast<T*>(base + S::W);
   double* t1 = reinterpret_cast<double*>(base + S::TR);
@@ -125,8 +127,35 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
         A[j * LD + i] = (T)v;
       }
     }
-    gsync<NT>();
-    jacobi_sym<T, D, LD, NT, true>(A, V, cs, redT, tid);
+    T* vs = reinterpret_cast<T*>(a.vstore) + p * D * D;
+    if (a.warm) {
+      // start from the previous eigenvectors: A <- V^T C V
+      for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = vs[e];
+      gsync<NT>();
+      for (int e = tid; e < D * D; e += NT) {
+        const int i = e / D, j = e % D;
+        T acc = T(0);
+#pragma unroll 4
+        for (int k = 0; k < D; ++k) acc += A[i * LD + k] * V[k * LD + j];
+        Wt[i * LD + j] = acc;
+      }
+      gsync<NT>();
+      for (int e = tid; e < D * D; e += NT) {
+        const int i = e / D, j = e % D;
+        if (i <= j) {
+          T acc = T(0);
+#pragma unroll 4
+          for (int k = 0; k < D; ++k) acc += V[k * LD + i] * Wt[k * LD + j];
+          A[i * LD + j] = acc;
+          A[j * LD + i] = acc;
+        }
+      }
+      gsync<NT>();
+      jacobi_sym<T, D, LD, NT, true, false>(A, V, cs, redT, tid);
+    } else {
+      jacobi_sym<T, D, LD, NT, true, true>(A, V, cs, redT, tid);
+    }
+    for (int e = tid; e < D * D; e += NT) vs[e] = V[(e / D) * LD + (e % D)];
     for (int k = tid; k < D; k += NT) {
       const T w = A[k * LD + k];
       W[k] = w > T(0) ? w : T(0);
@@ -188,6 +217,8 @@ cudaError_t launch_pair_t(const PairArgs& a, cudaStream_t s) {
   cudaError_t e = smem_once(k_pair<D, T>, smem, mask);
   if (e != cudaSuccess) return e;
   long blocks = (a.P + GPC - 1) / GPC;
+  const long res = resident_grid((const void*)k_pair<D, T>, NT * GPC, smem);
+  if (blocks > res) blocks = res;
   if (blocks < 1) blocks = 1;
   k_pair<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(a);
   return cudaGetLastError();
@@ -291,6 +322,16 @@ __global__ void __launch_bounds__(256) k_status(const SmallArgs a) {
 }
 
 }  // namespace
+
+int resident_grid(const void* kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  if (sms < 1) sms = 1;
+  if (per < 1) per = 1;
+  return sms * per;
+}
 
 cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s) {
   switch (a.D) {

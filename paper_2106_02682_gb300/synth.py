@@ -70,6 +70,8 @@ WORKLOADS = {
     "tfim1d_L2_N4096": dict(lattice=(8192,), cluster=(2,), h=1.0, kind="tfim"),
     # the same chain at 4096 spins (2048 clusters)
     "tfim1d_L2_N2048": dict(lattice=(4096,), cluster=(2,), h=1.0, kind="tfim"),
+    # the paper's table instance: TFI 100 x 1 periodic, h = 1, 2 x 1 clusters (50 clusters)
+    "tfim1d_L2_N50": dict(lattice=(100,), cluster=(2,), h=1.0, kind="tfim"),
     # 1-D TFI chain, 16 spins, single-spin clusters (4 x 4 pair marginals)
     "tfim1d_L1_N16": dict(lattice=(16,), cluster=(1,), h=1.0, kind="tfim"),
     # 2-D square lattice 64 x 64, h = 3, 2 x 1 clusters (16 x 16 pair marginals), 32 x 64 clusters
