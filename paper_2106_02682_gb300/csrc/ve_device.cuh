@@ -117,8 +117,11 @@ __device__ __forceinline__ void sym_schur2<float>(float app, float aqq, float ap
   const float tau = (aqq - app) / (2.f * apq);
   const float at = fabsf(tau);
   const float t = (at > JacobiTol<float>::big) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
-  c = rsqrtf(1.f + t * t);
-  s = t * c;
+  const float u = fmaf(t, t, 1.f);  // in [1, 2]
+  float y = rsqrtf(u);
+  y = y * fmaf(-0.5f * u, y * y, 1.5f);  // one Newton step: c^2 + s^2 = 1 to float rounding
+  c = y;
+  s = t * y;
 }
 
 // 2^-e for the float64 exponent e of x (x finite, nonzero): scales x into [1, 2).  The
@@ -171,11 +174,17 @@ __device__ __forceinline__ void unit_phase(T br, T bi, T& mag, T& wr, T& wi);
 
 template <>
 __device__ __forceinline__ void unit_phase<float>(float br, float bi, float& mag, float& wr, float& wi) {
-  const float q = br * br + bi * bi;
-  const float r = rsqrtf(q);
-  mag = q * r;
-  wr = br * r;
-  wi = -bi * r;
+  // scale into [1, 2) by a power of two first: squares of tiny entries would underflow
+  int ex = (__float_as_int(fmaxf(fabsf(br), fabsf(bi))) >> 23) & 0xff;
+  ex = ex < 1 ? 1 : (ex > 253 ? 253 : ex);
+  const float sc = __int_as_float((254 - ex) << 23), isc = __int_as_float(ex << 23);
+  const float xr = br * sc, xi = bi * sc;
+  const float q = fmaf(xr, xr, xi * xi);
+  float y = rsqrtf(q);
+  y = y * fmaf(-0.5f * q, y * y, 1.5f);
+  wr = xr * y;
+  wi = -xi * y;
+  mag = (q * y) * isc;
 }
 
 template <>
