@@ -146,6 +146,7 @@ struct ve_handle {
   size_t state_bytes = 0;
   double *state = nullptr, *rho0 = nullptr, *rt = nullptr, *lam = nullptr, *lam1 = nullptr,
          *lam2 = nullptr, *X = nullptr;
+  double* rho0_partial = nullptr;
   double *a1r = nullptr, *a2r = nullptr, *part = nullptr, *part2 = nullptr, *hb = nullptr,
          *H0 = nullptr, *lmin_pairs = nullptr, *lmin_k = nullptr, *lmin0 = nullptr;
   int *hslot = nullptr, *neg = nullptr, *canon = nullptr;
@@ -221,6 +222,7 @@ SmallArgs small_args(ve_handle* h) {
   a.part = h->part;
   a.part2 = h->part2;
   a.st = h->dst;
+  a.rho0_partial = h->rho0_partial;
   return a;
 }
 
@@ -244,12 +246,14 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
   if ((e = launch_status(sa, s)) != cudaSuccess) return e;
   if ((e = mark(4)) != cudaSuccess) return e;
   double2* spec = nullptr;
-  if ((e = fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, s)) != cudaSuccess) return e;
+  if ((e = fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, fp32, s)) != cudaSuccess)
+    return e;
   if ((e = mark(5)) != cudaSuccess) return e;
   if ((e = launch_xproj(h->plan, spec, h->canon, fp32, h->vk[v], warm ? 1 : 0, s)) != cudaSuccess)
     return e;
   if ((e = mark(6)) != cudaSuccess) return e;
-  if ((e = fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, s)) != cudaSuccess) return e;
+  if ((e = fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, fp32, s)) != cudaSuccess)
+    return e;
   return mark(7);
 }
 
@@ -440,6 +444,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   const size_t o_a2r = take(sizeof(double) * P * mm);
   const size_t o_part = take(sizeof(double) * 2 * P);
   const size_t o_part2 = take(sizeof(double) * P);
+  const size_t o_r0p = take(sizeof(double) * 128 * mm);
   const size_t o_hb = take(sizeof(double) * (nb > 0 ? nb : 1) * DD);
   const size_t o_H0 = take(sizeof(double) * mm);
   const size_t o_lp = take(sizeof(double) * P);
@@ -479,6 +484,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   h->a2r = (double*)(base + o_a2r);
   h->part = (double*)(base + o_part);
   h->part2 = (double*)(base + o_part2);
+  h->rho0_partial = (double*)(base + o_r0p);
   h->hb = (double*)(base + o_hb);
   h->H0 = (double*)(base + o_H0);
   h->lmin_pairs = (double*)(base + o_lp);
@@ -542,7 +548,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
     return VE_ECUDA;
   }
   *h->hst = ds;
-  const int launches[VE_NSTAGE] = {1, 1, 1, 1, h->plan.npass, 1, h->plan.npass};
+  const int launches[VE_NSTAGE] = {1, 2, 1, 1, h->plan.npass, 1, h->plan.npass};
   for (int i = 0; i < VE_NSTAGE; ++i) h->stage_launches[i] = launches[i];
   *out = h;
   return VE_OK;
@@ -683,7 +689,7 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   const Model& md = h->md;
   const int N = md.N, P = h->P;
   double2* spec = nullptr;
-  VE_CU(fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, h->stream));
+  VE_CU(fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, false, h->stream));
   VE_CU(launch_xeig(h->plan, spec, h->canon, h->lmin_k, h->stream));
   BoundArgs b;
   b.N = N;
@@ -768,9 +774,10 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
   VE_CU(launch_fft_tables(p, tw, s));
   VE_CU(launch_canon_list(p, canon, s));
   double2* spec = nullptr;
-  VE_CU(fft_forward(p, x_in, A, B, tw, &spec, s));
-  VE_CU(launch_xproj(p, spec, canon, precision == VE_PREC_MIXED, nullptr, 0, s));
-  VE_CU(fft_inverse(p, spec, A, B, x_out, tw, s));
+  const bool fp32 = precision == VE_PREC_MIXED;
+  VE_CU(fft_forward(p, x_in, A, B, tw, &spec, fp32, s));
+  VE_CU(launch_xproj(p, spec, canon, fp32, nullptr, 0, s));
+  VE_CU(fft_inverse(p, spec, A, B, x_out, tw, fp32, s));
   return VE_OK;
 }
 

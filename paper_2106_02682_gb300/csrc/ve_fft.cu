@@ -25,8 +25,25 @@ namespace ve {
 
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+template <typename R>
+struct C2;
+template <>
+struct C2<double> {
+  using type = double2;
+  static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
+};
+template <>
+struct C2<float> {
+  using type = float2;
+  static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+};
+
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) {
+  V r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
 }
 
 __device__ __forceinline__ int bitrev(int j, int logn) { return (int)(__brev((unsigned)j) >> (32 - logn)); }
@@ -34,11 +51,16 @@ __device__ __forceinline__ int bitrev(int j, int logn) { return (int)(__brev((un
 constexpr int FFT_EC = 32;        // entries per CTA
 constexpr int FFT_THREADS = 256;
 
+// One pass in precision R (double or float): the spectrum buffers hold C2<R>::type; the real
+// first block row (xin / xout) is always float64.  Twiddles are float64 tables, rounded to R.
+template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS)
-    k_fft_pass(const double* __restrict__ xin, const double2* __restrict__ cin, double2* cout,
-               double* xout, const FftPass ps, const int dir, const int E,
-               const double2* __restrict__ tw) {
-  extern __shared__ __align__(16) double2 sbuf[];
+    k_fft_pass(const double* __restrict__ xin, const typename C2<R>::type* __restrict__ cin,
+               typename C2<R>::type* cout, double* xout, const FftPass ps, const int dir,
+               const int E, const double2* __restrict__ tw) {
+  using V = typename C2<R>::type;
+  extern __shared__ __align__(16) unsigned char sraw[];
+  V* sbuf = reinterpret_cast<V*>(sraw);
   const int line = blockIdx.x;
   const int la = line / ps.B, lb = line % ps.B;
   const int e0 = blockIdx.y * FFT_EC;
@@ -50,10 +72,10 @@ __global__ void __launch_bounds__(FFT_THREADS)
     const int j = idx / FFT_EC, e = idx % FFT_EC;
     if (e >= ec) continue;
     const long slot = ((long)la * n + j) * ps.B + lb;
-    double2 v;
+    V v;
     if (xin) {
-      v.x = xin[slot * 2 * E + e0 + e];
-      v.y = xin[slot * 2 * E + E + e0 + e];
+      v.x = (R)xin[slot * 2 * E + e0 + e];
+      v.y = (R)xin[slot * 2 * E + E + e0 + e];
     } else {
       v = cin[slot * E + e0 + e];
     }
@@ -62,7 +84,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
   }
   __syncthreads();
   const double2* Wn = tw + ps.w_off;  // exp(-2 pi i t / n)
-  const double2* res = sbuf;
+  const V* res = sbuf;
+  const R sg = dir > 0 ? R(-1) : R(1);
   if (pow2) {
     for (int half = 1; half < n; half <<= 1) {
       const int stride = n / (2 * half);
@@ -70,24 +93,23 @@ __global__ void __launch_bounds__(FFT_THREADS)
         const int e = idx % FFT_EC, bf = idx / FFT_EC;
         const int grp = bf / half, j = bf % half;
         const int i0 = grp * 2 * half + j, i1 = i0 + half;
-        double2 w = Wn[j * stride];
-        if (dir > 0) w.y = -w.y;
-        const double2 u = sbuf[i0 * FFT_EC + e];
-        const double2 t = cmul(w, sbuf[i1 * FFT_EC + e]);
-        sbuf[i0 * FFT_EC + e] = make_double2(u.x + t.x, u.y + t.y);
-        sbuf[i1 * FFT_EC + e] = make_double2(u.x - t.x, u.y - t.y);
+        const double2 wd = Wn[j * stride];
+        const V w = C2<R>::make((R)wd.x, sg * (R)wd.y);
+        const V u = sbuf[i0 * FFT_EC + e];
+        const V t = cmul(w, sbuf[i1 * FFT_EC + e]);
+        sbuf[i0 * FFT_EC + e] = C2<R>::make(u.x + t.x, u.y + t.y);
+        sbuf[i1 * FFT_EC + e] = C2<R>::make(u.x - t.x, u.y - t.y);
       }
       __syncthreads();
     }
   } else {
-    double2* obuf = sbuf + n * FFT_EC;
+    V* obuf = sbuf + n * FFT_EC;
     for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
       const int k = idx / FFT_EC, e = idx % FFT_EC;
-      double2 acc = make_double2(0.0, 0.0);
+      V acc = C2<R>::make(R(0), R(0));
       for (int j = 0; j < n; ++j) {
-        double2 w = Wn[(j * k) % n];
-        if (dir > 0) w.y = -w.y;
-        const double2 t = cmul(w, sbuf[j * FFT_EC + e]);
+        const double2 wd = Wn[(j * k) % n];
+        const V t = cmul(C2<R>::make((R)wd.x, sg * (R)wd.y), sbuf[j * FFT_EC + e]);
         acc.x += t.x;
         acc.y += t.y;
       }
@@ -99,17 +121,16 @@ __global__ void __launch_bounds__(FFT_THREADS)
   for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
     const int k = idx / FFT_EC, e = idx % FFT_EC;
     if (e >= ec) continue;
-    double2 v = res[idx];
+    V v = res[idx];
     if (ps.tw_mode) {
       const int other = (ps.tw_mode == 1) ? lb : la;
-      double2 w = tw[ps.tw_off + (int)(((long)k * other) % ps.twN)];
-      if (dir > 0) w.y = -w.y;
-      v = cmul(v, w);
+      const double2 wd = tw[ps.tw_off + (int)(((long)k * other) % ps.twN)];
+      v = cmul(v, C2<R>::make((R)wd.x, sg * (R)wd.y));
     }
     const long slot = ((long)la * n + k) * ps.B + lb;
     if (xout) {
-      xout[slot * 2 * E + e0 + e] = v.x;
-      xout[slot * 2 * E + E + e0 + e] = v.y;
+      xout[slot * 2 * E + e0 + e] = (double)v.x;
+      xout[slot * 2 * E + E + e0 + e] = (double)v.y;
     } else {
       cout[slot * E + e0 + e] = v;
     }
@@ -149,20 +170,21 @@ struct XSmem {
 };
 
 // Unpack block C_k (unnormalised) of slot s from the packed spectrum into (Ar, Ai), Hermitised.
-template <int D, int NT, int LD, typename T>
-__device__ void unpack_block(const double2* spec, int s, int s2, int E, T* Ar, T* Ai, int tid) {
+template <int D, int NT, int LD, typename T, typename V>
+__device__ void unpack_block(const V* spec, int s, int s2, int E, T* Ar, T* Ai, int tid) {
+  using R = decltype(V{}.x);
   for (int f = tid; f < D * D; f += NT) {
     const int e = f < E ? f : f - E;
-    const double2 z = spec[(long)s * E + e];
-    const double2 zz = spec[(long)s2 * E + e];  // conj taken below
-    double cr, ci;
+    const V z = spec[(long)s * E + e];
+    const V zz = spec[(long)s2 * E + e];  // conj taken below
+    R cr, ci;
     if (f < E) {  // (z + conj(zz)) / 2
-      cr = 0.5 * (z.x + zz.x);
-      ci = 0.5 * (z.y - zz.y);
+      cr = R(0.5) * (z.x + zz.x);
+      ci = R(0.5) * (z.y - zz.y);
     } else {      // (z - conj(zz)) / (2i)
-      const double dr = z.x - zz.x, di = z.y + zz.y;
-      cr = 0.5 * di;
-      ci = -0.5 * dr;
+      const R dr = z.x - zz.x, di = z.y + zz.y;
+      cr = R(0.5) * di;
+      ci = R(-0.5) * dr;
     }
     Ar[(f / D) * LD + (f % D)] = (T)cr;
     Ai[(f / D) * LD + (f % D)] = (T)ci;
@@ -186,8 +208,8 @@ __device__ void unpack_block(const double2* spec, int s, int s2, int E, T* Ar, T
 
 template <int D, typename T>
 __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
-    k_xproj(double2* spec, const int* __restrict__ canon, const int ncanon, const FftPlan p,
-            const double invN, T* vstore, const int warm) {
+    k_xproj(typename C2<T>::type* spec, const int* __restrict__ canon, const int ncanon,
+            const FftPlan p, const double invN, T* vstore, const int warm) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
   constexpr int GPC = (NT == 32) ? 4 : 1;
   using S = XSmem<D, T>;
@@ -282,14 +304,15 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
     }
     gsync<NT>();
     // pack Y_k (and Y_{-k} = conj Y_k) back, scaled by 1/N
+    const T sc = (T)invN;
     for (int e = tid; e < E; e += NT) {
       const int f1 = e, f2 = e + E;
-      const double y1r = (double)Ar[(f1 / D) * LD + f1 % D] * invN;
-      const double y1i = (double)Ai[(f1 / D) * LD + f1 % D] * invN;
-      const double y2r = (double)Ar[(f2 / D) * LD + f2 % D] * invN;
-      const double y2i = (double)Ai[(f2 / D) * LD + f2 % D] * invN;
-      spec[(long)s * E + e] = make_double2(y1r - y2i, y1i + y2r);
-      if (s2 != s) spec[(long)s2 * E + e] = make_double2(y1r + y2i, -y1i + y2r);
+      const T y1r = Ar[(f1 / D) * LD + f1 % D] * sc;
+      const T y1i = Ai[(f1 / D) * LD + f1 % D] * sc;
+      const T y2r = Ar[(f2 / D) * LD + f2 % D] * sc;
+      const T y2i = Ai[(f2 / D) * LD + f2 % D] * sc;
+      spec[(long)s * E + e] = C2<T>::make(y1r - y2i, y1i + y2r);
+      if (s2 != s) spec[(long)s2 * E + e] = C2<T>::make(y1r + y2i, -y1i + y2r);
     }
     gsync<NT>();
   }
@@ -359,8 +382,9 @@ cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, vo
   long blocks = (nc + GPC - 1) / GPC;
   const long res = resident_grid((const void*)k_xproj<D, T>, NT * GPC, smem);
   if (blocks > res) blocks = res;
-  k_xproj<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(spec, canon, nc, p, 1.0 / p.N,
-                                                          reinterpret_cast<T*>(vstore), warm);
+  k_xproj<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(
+      reinterpret_cast<typename C2<T>::type*>(spec), canon, nc, p, 1.0 / p.N,
+      reinterpret_cast<T*>(vstore), warm);
   return cudaGetLastError();
 }
 
@@ -380,17 +404,27 @@ cudaError_t launch_xeig_t(const FftPlan& p, const double2* spec, const int* cano
   return cudaGetLastError();
 }
 
-cudaError_t run_pass(const FftPlan& p, const FftPass& ps, int dir, const double* xin,
-                     const double2* cin, double2* cout, double* xout, const double2* tw,
-                     cudaStream_t s) {
+template <typename R>
+cudaError_t run_pass_t(const FftPlan& p, const FftPass& ps, int dir, const double* xin,
+                       const void* cin, void* cout, double* xout, const double2* tw,
+                       cudaStream_t s) {
+  using V = typename C2<R>::type;
   const bool pow2 = (ps.n & (ps.n - 1)) == 0;
-  const size_t smem = sizeof(double2) * ps.n * FFT_EC * (pow2 ? 1 : 2);
+  const size_t smem = sizeof(V) * ps.n * FFT_EC * (pow2 ? 1 : 2);
   static unsigned long long mask = 0;
-  cudaError_t e = smem_once(k_fft_pass, 2 * sizeof(double2) * 64 * FFT_EC, mask);
+  cudaError_t e = smem_once(k_fft_pass<R>, 2 * sizeof(V) * 64 * FFT_EC, mask);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(ps.A * ps.B), (unsigned)((p.E + FFT_EC - 1) / FFT_EC));
-  k_fft_pass<<<grid, FFT_THREADS, smem, s>>>(xin, cin, cout, xout, ps, dir, p.E, tw);
+  k_fft_pass<R><<<grid, FFT_THREADS, smem, s>>>(xin, reinterpret_cast<const V*>(cin),
+                                                reinterpret_cast<V*>(cout), xout, ps, dir, p.E, tw);
   return cudaGetLastError();
+}
+
+cudaError_t run_pass(const FftPlan& p, const FftPass& ps, int dir, const double* xin,
+                     const void* cin, void* cout, double* xout, const double2* tw, bool fp32,
+                     cudaStream_t s) {
+  return fp32 ? run_pass_t<float>(p, ps, dir, xin, cin, cout, xout, tw, s)
+              : run_pass_t<double>(p, ps, dir, xin, cin, cout, xout, tw, s);
 }
 
 int smallest_factor_pair(int N, int& N1, int& N2) {
@@ -483,25 +517,25 @@ cudaError_t launch_fft_tables(const FftPlan& p, double2* tw, cudaStream_t s) {
 }
 
 cudaError_t fft_forward(const FftPlan& p, const double* x, double2* bufA, double2* bufB,
-                        const double2* tw, double2** spec, cudaStream_t s) {
-  cudaError_t e = run_pass(p, p.fwd[0], -1, x, nullptr, bufA, nullptr, tw, s);
+                        const double2* tw, double2** spec, bool fp32, cudaStream_t s) {
+  cudaError_t e = run_pass(p, p.fwd[0], -1, x, nullptr, bufA, nullptr, tw, fp32, s);
   if (e != cudaSuccess) return e;
   if (p.npass == 1) {
     *spec = bufA;
     return cudaSuccess;
   }
-  e = run_pass(p, p.fwd[1], -1, nullptr, bufA, bufB, nullptr, tw, s);
+  e = run_pass(p, p.fwd[1], -1, nullptr, bufA, bufB, nullptr, tw, fp32, s);
   *spec = bufB;
   return e;
 }
 
 cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2* bufB, double* x,
-                        const double2* tw, cudaStream_t s) {
-  if (p.npass == 1) return run_pass(p, p.inv[0], +1, nullptr, spec, nullptr, x, tw, s);
+                        const double2* tw, bool fp32, cudaStream_t s) {
+  if (p.npass == 1) return run_pass(p, p.inv[0], +1, nullptr, spec, nullptr, x, tw, fp32, s);
   double2* other = (spec == bufA) ? bufB : bufA;
-  cudaError_t e = run_pass(p, p.inv[0], +1, nullptr, spec, other, nullptr, tw, s);
+  cudaError_t e = run_pass(p, p.inv[0], +1, nullptr, spec, other, nullptr, tw, fp32, s);
   if (e != cudaSuccess) return e;
-  return run_pass(p, p.inv[1], +1, nullptr, other, nullptr, x, tw, s);
+  return run_pass(p, p.inv[1], +1, nullptr, other, nullptr, x, tw, fp32, s);
 }
 
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,

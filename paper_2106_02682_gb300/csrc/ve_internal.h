@@ -61,6 +61,7 @@ struct SmallArgs {
   const double* part;
   double* part2;  // P: ||A1 rho - rho0||^2 + ||A2 rho - rho0||^2
   DevStatus* st;
+  double* rho0_partial;  // 128 * m*m chunk sums of the rho_0 reduction
 };
 
 // Number of CTAs that keep every SM busy for a kernel with the given block shape.
@@ -68,6 +69,7 @@ int resident_grid(const void* kernel, int threads, size_t smem);
 
 // D in {4, 16, 64}; fp32 selects the float32 projection.
 cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s);
+// rho_0 update: two launches (chunk sums over delta, then one CTA), fixed reduction order.
 cudaError_t launch_rho0(const SmallArgs& a, cudaStream_t s);
 cudaError_t launch_dual12(const SmallArgs& a, cudaStream_t s);
 cudaError_t launch_status(const SmallArgs& a, cudaStream_t s);
@@ -96,16 +98,18 @@ struct FftPlan {
 int fft_plan_build(FftPlan& p, int dim, const int M[2], int D);
 cudaError_t launch_fft_tables(const FftPlan& p, double2* tw, cudaStream_t s);
 // Forward: real first block row x (N*D*D) -> spectrum (returned pointer is bufA or bufB).
+// fp32: the spectrum is float2 (the buffers are reinterpreted) and the passes run in float32.
 cudaError_t fft_forward(const FftPlan& p, const double* x, double2* bufA, double2* bufB,
-                        const double2* tw, double2** spec, cudaStream_t s);
+                        const double2* tw, double2** spec, bool fp32, cudaStream_t s);
 // Inverse: spectrum (in `spec`, which is bufA or bufB) -> real first block row x.
 cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2* bufB, double* x,
-                        const double2* tw, cudaStream_t s);
+                        const double2* tw, bool fp32, cudaStream_t s);
 // List of the canonical spectrum slots (s <= slot of -k), ncanon of them, in increasing order.
 cudaError_t launch_canon_list(const FftPlan& p, int* canon, cudaStream_t s);
 int fft_ncanon(const FftPlan& p);
-// Per-wavevector projection in place on the spectrum, scaled by 1/N.  vstore (N * 2 * D*D of
-// float or double, or null): eigenvectors kept per slot; warm = 1 starts from them.
+// Per-wavevector projection in place on the spectrum, scaled by 1/N; fp32 = float2 spectrum and
+// float32 eigensolve.  vstore (N * 2 * D*D of float or double, or null): eigenvectors kept per
+// slot; warm = 1 starts from them.
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
                          void* vstore, int warm, cudaStream_t s);
 // lmin[slot] = smallest eigenvalue of the (unnormalised) block C_k, +inf for non-canonical slots.

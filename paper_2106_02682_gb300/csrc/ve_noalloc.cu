@@ -66,9 +66,9 @@ extern "C" int ve_circulant_project_noalloc(const double* x_in, double* x_out, i
   if (launch_fft_tables(p, tw, s) != cudaSuccess) return VE_ECUDA;
   if (launch_canon_list(p, canon, s) != cudaSuccess) return VE_ECUDA;
   double2* spec = nullptr;
-  if (fft_forward(p, x_in, A, B, tw, &spec, s) != cudaSuccess) return VE_ECUDA;
-  if (launch_xproj(p, spec, canon, precision == VE_PREC_MIXED, nullptr, 0, s) != cudaSuccess)
-    return VE_ECUDA;
-  if (fft_inverse(p, spec, A, B, x_out, tw, s) != cudaSuccess) return VE_ECUDA;
+  const bool fp32 = precision == VE_PREC_MIXED;
+  if (fft_forward(p, x_in, A, B, tw, &spec, fp32, s) != cudaSuccess) return VE_ECUDA;
+  if (launch_xproj(p, spec, canon, fp32, nullptr, 0, s) != cudaSuccess) return VE_ECUDA;
+  if (fft_inverse(p, spec, A, B, x_out, tw, fp32, s) != cudaSuccess) return VE_ECUDA;
   return VE_OK;
 }

@@ -29,20 +29,21 @@ struct PairShape {
 template <int D, typename T>
 struct PairSmem {
   static constexpr int m = PairShape<D>::m, LD = PairShape<D>::LD;
+  static constexpr size_t al(size_t x) { return ((x + 15) / 16) * 16; }
   // per group, in bytes; every array 16-byte aligned
-  static constexpr size_t R = 0;                                      // double D*D
-  static constexpr size_t Xs = R + sizeof(double) * D * D;           // double D*D
-  static constexpr size_t A = Xs + sizeof(double) * D * D;           // T D*LD
-  static constexpr size_t V = A + ((sizeof(T) * D * LD + 15) / 16) * 16;
-  static constexpr size_t WT = V + ((sizeof(T) * D * LD + 15) / 16) * 16;  // T D*LD
-  static constexpr size_t CS = WT + ((sizeof(T) * D * LD + 15) / 16) * 16;  // T D
-  static constexpr size_t W = CS + ((sizeof(T) * D + 15) / 16) * 16;       // T D
-  static constexpr size_t TR = W + ((sizeof(T) * D + 15) / 16) * 16;       // double 2*m*m + 2
-  static constexpr size_t RED = TR + ((sizeof(double) * (2 * m * m + 2) + 15) / 16) * 16;
-  static constexpr size_t REDT = RED + sizeof(double) * 8;
-  static constexpr size_t bytes = REDT + ((sizeof(T) * 8 + 15) / 16) * 16;
+  static constexpr size_t R = 0;                                   // T D*D  (rhs, then rho)
+  static constexpr size_t Xs = R + al(sizeof(T) * D * D);          // T D*D  (X_{0,delta})
+  static constexpr size_t A = Xs + al(sizeof(T) * D * D);          // T D*LD
+  static constexpr size_t V = A + al(sizeof(T) * D * LD);
+  static constexpr size_t WT = V + al(sizeof(T) * D * LD);         // T D*LD
+  static constexpr size_t CS = WT + al(sizeof(T) * D * LD);        // T D
+  static constexpr size_t W = CS + al(sizeof(T) * D);              // T D
+  static constexpr size_t TR = W + al(sizeof(T) * D);              // T 2*m*m + 2
+  static constexpr size_t RED = TR + al(sizeof(T) * (2 * m * m + 2));
+  static constexpr size_t bytes = RED + al(sizeof(T) * 8);
 };
 
+// Arithmetic in T (double, or float in the mixed-precision sweep); the state stays float64.
 template <int D, typename T>
 __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
     k_pair(const PairArgs a) {
@@ -52,21 +53,21 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
   unsigned char* base = smem_raw + (size_t)g * S::bytes;
-  double* R = reinterpret_cast<double*>(base + S::R);
-  double* Xs = reinterpret_cast<double*>(base + S::Xs);
+  T* R = reinterpret_cast<T*>(base + S::R);
+  T* Xs = reinterpret_cast<T*>(base + S::Xs);
   T* A = reinterpret_cast<T*>(base + S::A);
   T* V = reinterpret_cast<T*>(base + S::V);
   T* Wt = reinterpret_cast<T*>(base + S::WT);
   T* cs = reinterpret_cast<T*>(base + S::CS);
   T* W = reinterpret_cast<T*>(base + S::W);
-  double* t1 = reinterpret_cast<double*>(base + S::TR);
-  double* t2 = t1 + m * m;
-  double* red = reinterpret_cast<double*>(base + S::RED);
-  T* redT = reinterpret_cast<T*>(base + S::REDT);
+  T* t1 = reinterpret_cast<T*>(base + S::TR);
+  T* t2 = t1 + m * m;
+  T* red = reinterpret_cast<T*>(base + S::RED);
 
-  const double mu = a.mu, nu = a.nu, eps = a.eps;
-  const double alpha = nu * m;
-  const double c0 = 1.0 / mu, c1 = 1.0 / (mu + alpha), c2 = 1.0 / (mu + 2.0 * alpha);
+  const T mu = (T)a.mu, nu = (T)a.nu, eps = (T)a.eps;
+  const T alpha = nu * m;
+  const T c0 = T(1) / mu, c1 = T(1) / (mu + alpha), c2 = T(1) / (mu + T(2) * alpha);
+  const T imu = T(1) / mu;
 
   for (long p = (long)blockIdx.x * GPC + g; p < a.P; p += (long)gridDim.x * GPC) {
     const long dl = p + 1;  // linear cluster offset delta
@@ -78,25 +79,25 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
     const int hs = a.hslot[dl];
     const double* Hb = hs >= 0 ? a.hb + (long)hs * D * D : nullptr;
 
-    for (int e = tid; e < D * D; e += NT) Xs[e] = Xb[e];
+    for (int e = tid; e < D * D; e += NT) Xs[e] = (T)Xb[e];
     gsync<NT>();
     // right-hand side of Eq. (rhoijUpdate) with H' of Eq. (effHam)
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
       const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
-      const double h = Hb ? Hb[e] : 0.0;
+      const T h = Hb ? (T)Hb[e] : T(0);
       // (R^* X)_{(a,b),(c,d)} = X_{(a,c),(d,b)} and its transpose X_{(c,a),(b,d)}
-      const double hp = h - Xs[(pa * m + pc) * D + (pd * m + pb)] - Xs[(pc * m + pa) * D + (pb * m + pd)];
-      double y = mu * rt[e] + lam[e] - hp;
-      if (pb == pd) y += nu * a.rho0[pa * m + pc] - l1[pa * m + pc];
-      if (pa == pc) y += nu * a.rho0[pb * m + pd] - l2[pb * m + pd];
+      const T hp = h - Xs[(pa * m + pc) * D + (pd * m + pb)] - Xs[(pc * m + pa) * D + (pb * m + pd)];
+      T y = mu * (T)rt[e] + (T)lam[e] - hp;
+      if (pb == pd) y += nu * (T)a.rho0[pa * m + pc] - (T)l1[pa * m + pc];
+      if (pa == pc) y += nu * (T)a.rho0[pb * m + pd] - (T)l2[pb * m + pd];
       R[e] = y;
     }
     gsync<NT>();
     // partial traces of the right-hand side
     for (int idx = tid; idx < m * m; idx += NT) {
       const int x = idx / m, z = idx % m;
-      double s1 = 0.0, s2 = 0.0;
+      T s1 = T(0), s2 = T(0);
       for (int k = 0; k < m; ++k) {
         s1 += R[(x * m + k) * D + (z * m + k)];
         s2 += R[(k * m + x) * D + (k * m + z)];
@@ -105,28 +106,30 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
       t2[idx] = s2;
     }
     gsync<NT>();
-    double tr = 0.0;
+    T tr = T(0);
     for (int k = 0; k < m; ++k) tr += t1[k * m + k];
     // rho = (mu + nu A1^*A1 + nu A2^*A2)^{-1} rhs, closed form on the projectors P1, P2, Q
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
       const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
-      const double y = R[e];
-      const double P1 = (pb == pd) ? t1[pa * m + pc] / m : 0.0;
-      const double P2 = (pa == pc) ? t2[pb * m + pd] / m : 0.0;
-      const double Q = (i == j) ? tr / D : 0.0;
-      R[e] = (y - P1 - P2 + Q) * c0 + (P1 + P2 - 2.0 * Q) * c1 + Q * c2;
+      const T y = R[e];
+      const T P1 = (pb == pd) ? t1[pa * m + pc] / m : T(0);
+      const T P2 = (pa == pc) ? t2[pb * m + pd] / m : T(0);
+      const T Q = (i == j) ? tr / D : T(0);
+      R[e] = (y - P1 - P2 + Q) * c0 + (P1 + P2 - T(2) * Q) * c1 + Q * c2;
     }
     gsync<NT>();
     // C = rho - Lambda / mu, symmetrised, into A
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
       if (i <= j) {
-        const double v = 0.5 * (R[i * D + j] + R[j * D + i]) - 0.5 * (lam[i * D + j] + lam[j * D + i]) / mu;
-        A[i * LD + j] = (T)v;
-        A[j * LD + i] = (T)v;
+        const T v = T(0.5) * (R[i * D + j] + R[j * D + i]) -
+                    T(0.5) * ((T)lam[i * D + j] + (T)lam[j * D + i]) * imu;
+        A[i * LD + j] = v;
+        A[j * LD + i] = v;
       }
     }
+    gsync<NT>();
     T* vs = reinterpret_cast<T*>(a.vstore) + p * D * D;
     if (a.warm) {
       // start from the previous eigenvectors: A <- V^T C V
@@ -151,9 +154,9 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
         }
       }
       gsync<NT>();
-      jacobi_sym<T, D, LD, NT, true, false>(A, V, cs, redT, tid);
+      jacobi_sym<T, D, LD, NT, true, false>(A, V, cs, red, tid);
     } else {
-      jacobi_sym<T, D, LD, NT, true, true>(A, V, cs, redT, tid);
+      jacobi_sym<T, D, LD, NT, true, true>(A, V, cs, red, tid);
     }
     for (int e = tid; e < D * D; e += NT) vs[e] = V[(e / D) * LD + (e % D)];
     for (int k = tid; k < D; k += NT) {
@@ -173,37 +176,37 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
       }
     }
     gsync<NT>();
-    double rr = 0.0, en = 0.0;
+    T rr = T(0), en = T(0);
     double* rtw = a.rt + p * D * D;
     double* lamw = a.lam + p * D * D;
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
       const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
-      const double rho = R[e];
-      const double rtn = (double)A[i * LD + j];
-      const double h = Hb ? Hb[e] : 0.0;
-      lamw[e] = lam[e] + mu * (rtn - rho);
-      rtw[e] = rtn;
+      const T rho = R[e];
+      const T rtn = A[i * LD + j];
+      const T h = Hb ? (T)Hb[e] : T(0);
+      lamw[e] = (double)((T)lam[e] + mu * (rtn - rho));
+      rtw[e] = (double)rtn;
       // X'_{0,delta} = X_{0,delta} - eps G_{0,delta}[rho], G entry (a,b),(c,d) = rho_{(a,d),(b,c)}
-      Xb[e] = Xs[e] - eps * R[(pa * m + pd) * D + (pb * m + pc)];
+      Xb[e] = (double)(Xs[e] - eps * R[(pa * m + pd) * D + (pb * m + pc)]);
       rr += (rho - rtn) * (rho - rtn);
       en += h * R[j * D + i];
     }
     for (int idx = tid; idx < m * m; idx += NT) {
       const int x = idx / m, z = idx % m;
-      double s1 = 0.0, s2 = 0.0;
+      T s1 = T(0), s2 = T(0);
       for (int k = 0; k < m; ++k) {
         s1 += R[(x * m + k) * D + (z * m + k)];
         s2 += R[(k * m + x) * D + (k * m + z)];
       }
-      a.a1r[p * m * m + idx] = s1;
-      a.a2r[p * m * m + idx] = s2;
+      a.a1r[p * m * m + idx] = (double)s1;
+      a.a2r[p * m * m + idx] = (double)s2;
     }
     rr = gsum<NT>(rr, red);
     en = gsum<NT>(en, red);
     if (tid == 0) {
-      a.part[p * 2 + 0] = rr;
-      a.part[p * 2 + 1] = en;
+      a.part[p * 2 + 0] = (double)rr;
+      a.part[p * 2 + 1] = (double)en;
     }
     gsync<NT>();
   }
@@ -224,27 +227,42 @@ cudaError_t launch_pair_t(const PairArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- rho_0 and X'_00 (one CTA)
-__global__ void __launch_bounds__(256) k_rho0(const SmallArgs a) {
+// ---------------------------------------------------------------- rho_0 and X'_00
+// Stage 1: RHO0_CHUNKS CTAs each sum a contiguous range of offsets delta of
+// nu A1[rho_{0,delta}] + Lambda1_{0,delta} (m*m entries); stage 2 (one CTA) adds the chunk sums
+// in order.  Both orders are fixed, so the result is reproducible bit for bit.
+constexpr int RHO0_CHUNKS = 128;
+
+__global__ void __launch_bounds__(256) k_rho0_partial(const SmallArgs a, double* partial) {
+  const int mm = a.m * a.m;
+  const long per = (a.P + RHO0_CHUNKS - 1) / RHO0_CHUNKS;
+  const long lo = blockIdx.x * per, hi = min((long)a.P, lo + per);
+  // threads: (entry, sub-range) with 256 / mm sub-ranges per chunk
+  const int subs = 256 / mm;
   __shared__ double S[256];
-  __shared__ double rp[64];
-  __shared__ double red[8];
-  const int m = a.m, mm = m * m, D = a.D, P = a.P;
   const int t = threadIdx.x;
-  const int chunks = 256 / mm;  // m*m in {4, 16, 64}
-  // sum_delta (nu A1[rho_{0,delta}] + Lambda1_{0,delta}), chunked over delta in fixed order
-  if (t < chunks * mm) {
+  double acc = 0.0;
+  if (t < subs * mm) {
     const int idx = t % mm, c = t / mm;
-    const long per = (P + chunks - 1) / chunks;
-    const long lo = c * per, hi = min((long)P, lo + per);
-    double s = 0.0;
-    for (long p = lo; p < hi; ++p) s += a.nu * a.a1r[p * mm + idx] + a.lam1[p * mm + idx];
-    S[t] = s;
+    for (long p = lo + c; p < hi; p += subs) acc += a.nu * a.a1r[p * mm + idx] + a.lam1[p * mm + idx];
   }
+  S[t] = acc;
   __syncthreads();
   if (t < mm) {
     double s = 0.0;
-    for (int c = 0; c < chunks; ++c) s += S[c * mm + t];
+    for (int c = 0; c < subs; ++c) s += S[c * mm + t];
+    partial[blockIdx.x * mm + t] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rho0(const SmallArgs a, const double* partial) {
+  __shared__ double rp[64];
+  __shared__ double red[8];
+  const int m = a.m, mm = m * m, D = a.D;
+  const int t = threadIdx.x;
+  if (t < mm) {
+    double s = 0.0;
+    for (int c = 0; c < RHO0_CHUNKS; ++c) s += partial[c * mm + t];
     // H'_0 = H_0 - sum_a X_{(a,b),(a,d)}  (Eq. (effHam) with matrix units)
     const int b = t / m, d = t % m;
     double hx = 0.0;
@@ -256,6 +274,7 @@ __global__ void __launch_bounds__(256) k_rho0(const SmallArgs a) {
   double tr = 0.0;
   for (int k = 0; k < m; ++k) tr += rp[k * m + k];
   const double z = (1.0 - tr) / m;
+  __syncthreads();
   if (t < mm) {
     const int b = t / m, d = t % m;
     rp[t] = rp[t] + (b == d ? z : 0.0);
@@ -343,7 +362,10 @@ cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s) {
 }
 
 cudaError_t launch_rho0(const SmallArgs& a, cudaStream_t s) {
-  k_rho0<<<1, 256, 0, s>>>(a);
+  k_rho0_partial<<<RHO0_CHUNKS, 256, 0, s>>>(a, a.rho0_partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rho0<<<1, 256, 0, s>>>(a, a.rho0_partial);
   return cudaGetLastError();
 }
 
