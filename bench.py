@@ -251,6 +251,7 @@ def run_ours(args):
         ck = clocks.stop()
         total_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
         prof = ve.ve_profile_read(h)
+        jac_pair, jac_k = ve.ve_profile_sweeps(h)
         ve.ve_profile(h, 0)
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         if world > 1:
@@ -348,6 +349,7 @@ def run_ours(args):
             "config": workload_config(args, N, D),
             "e2e": e2e, "gpu_launches": launches * world, "roofline": roof, "stages": stages,
             "clocks": ck, "time_to_bound": ttb,
+            "jacobi_sweeps_per_eigensolve": {"pair": jac_pair, "wavevector": jac_k},
             "last_status": {"iter": status.iter, "energy_per_spin": status.energy_per_spin,
                             "feas_err": status.feas_err},
         }

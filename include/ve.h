@@ -157,6 +157,9 @@ int ve_get_status(ve_handle* h, ve_status* out);
 #define VE_NSTAGE 7
 int ve_profile(ve_handle* h, int enable);
 int ve_profile_read(ve_handle* h, double* ms, long* launches);
+/* Mean Jacobi sweeps per eigensolve over the profiled sweeps: pair projections (*pair) and
+ * wavevector projections (*wavevector); 0 if none ran.  Errors: VE_EINVAL, VE_ECUDA. */
+int ve_profile_sweeps(ve_handle* h, double* pair, double* wavevector);
 
 /* Name of a status code (static string). */
 const char* ve_error_string(int code);

@@ -165,6 +165,7 @@ struct ve_handle {
   bool prof = false;
   cudaEvent_t ev[VE_NSTAGE + 1] = {};
   double prof_ms[VE_NSTAGE] = {};
+  unsigned long long* jstats = nullptr;  // device: pair sweeps, pair matrices, k sweeps, k matrices
   long prof_launch[VE_NSTAGE] = {};
   int stage_launches[VE_NSTAGE] = {};
 };
@@ -233,6 +234,7 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
   PairArgs pa = pair_args(h);
   pa.vstore = h->vpair[v];
   pa.warm = warm ? 1 : 0;
+  pa.stats = h->prof ? h->jstats : nullptr;
   const SmallArgs sa = small_args(h);
   cudaError_t e;
   auto mark = [&](int i) { return h->prof ? cudaEventRecord(h->ev[i], s) : cudaSuccess; };
@@ -249,7 +251,8 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
   if ((e = fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, fp32, s)) != cudaSuccess)
     return e;
   if ((e = mark(5)) != cudaSuccess) return e;
-  if ((e = launch_xproj(h->plan, spec, h->canon, fp32, h->vk[v], warm ? 1 : 0, s)) != cudaSuccess)
+  if ((e = launch_xproj(h->plan, spec, h->canon, fp32, h->vk[v], warm ? 1 : 0, s,
+                       h->prof ? h->jstats + 2 : nullptr)) != cudaSuccess)
     return e;
   if ((e = mark(6)) != cudaSuccess) return e;
   if ((e = fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, fp32, s)) != cudaSuccess)
@@ -461,6 +464,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   const size_t o_sb = take(sizeof(double2) * N * h->plan.E);
   const size_t o_tw = take(sizeof(double2) * h->plan.ntw);
   const size_t o_st = take(sizeof(DevStatus));
+  const size_t o_js = take(sizeof(unsigned long long) * 4);
   if (cudaMalloc(&h->dev, off) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -502,6 +506,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   h->specB = (double2*)(base + o_sb);
   h->tw = (double2*)(base + o_tw);
   h->dst = (DevStatus*)(base + o_st);
+  h->jstats = (unsigned long long*)(base + o_js);
   if (h->opt.stream) {
     h->stream = (cudaStream_t)h->opt.stream;
   } else {
@@ -615,8 +620,21 @@ int ve_profile(ve_handle* h, int enable) {
       h->prof_ms[i] = 0.0;
       h->prof_launch[i] = 0;
     }
+    VE_CU(cudaMemsetAsync(h->jstats, 0, sizeof(unsigned long long) * 4, h->stream));
+    VE_CU(cudaStreamSynchronize(h->stream));
   }
   h->prof = enable != 0;
+  return VE_OK;
+}
+
+int ve_profile_sweeps(ve_handle* h, double* pair, double* wavevector) {
+  if (!h || !pair || !wavevector) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  unsigned long long c[4] = {0, 0, 0, 0};
+  VE_CU(cudaMemcpyAsync(c, h->jstats, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+  VE_CU(cudaStreamSynchronize(h->stream));
+  *pair = c[1] ? (double)c[0] / (double)c[1] : 0.0;
+  *wavevector = c[3] ? (double)c[2] / (double)c[3] : 0.0;
   return VE_OK;
 }
 

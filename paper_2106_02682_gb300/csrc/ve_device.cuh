@@ -205,8 +205,9 @@ __device__ __forceinline__ void unit_phase<double>(double br, double bi, double&
 
 // Real symmetric Jacobi on A (n x n, leading dimension LD) in shared memory.  If VEC, V (same
 // layout) receives the eigenvectors.  cs: shared scratch of n entries; red: NT/32 entries.
+// Returns the number of sweeps performed.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
-__device__ void jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
+__device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
   constexpr int H = n / 2;
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
@@ -218,7 +219,8 @@ __device__ void jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
     for (int e = tid; e < n * n; e += NT) V[(e / n) * LD + (e % n)] = (e / n == e % n) ? T(1) : T(0);
   }
   gsync<NT>();
-  for (int sweep = 0; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
+  int sweep = 0;
+  for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
     T off = T(0);
     for (int e = tid; e < n * n; e += NT) {
       const int i = e / n, j = e % n;
@@ -273,13 +275,15 @@ __device__ void jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
       gsync<NT>();
     }
   }
+  return sweep;
 }
 
 // Complex Hermitian Jacobi on (Ar, Ai).  For the pair (p, q) with a_pq = |b| e^{i phi} the
 // unitary U = diag(1, w) J, w = e^{-i phi}, J the real rotation of [[a_pp, |b|], [|b|, a_qq]],
 // diagonalises the 2x2 block; A <- U^H A U, V <- V U.  cs: shared scratch of 2n entries.
+// Returns the number of sweeps performed.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
-__device__ void jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
+__device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
   constexpr int H = n / 2;
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
@@ -295,7 +299,8 @@ __device__ void jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) 
     }
   }
   gsync<NT>();
-  for (int sweep = 0; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
+  int sweep = 0;
+  for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
     T off = T(0);
     for (int e = tid; e < n * n; e += NT) {
       const int i = e / n, j = e % n;
@@ -390,6 +395,7 @@ __device__ void jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) 
       gsync<NT>();
     }
   }
+  return sweep;
 }
 
 // Threads per group and leading dimension used for an n x n matrix.

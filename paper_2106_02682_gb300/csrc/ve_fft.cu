@@ -48,7 +48,7 @@ __device__ __forceinline__ V cmul(V a, V b) {
 
 __device__ __forceinline__ int bitrev(int j, int logn) { return (int)(__brev((unsigned)j) >> (32 - logn)); }
 
-constexpr int FFT_EC = 32;        // entries per CTA
+constexpr int FFT_EC = 32;        // largest number of entries per CTA
 constexpr int FFT_THREADS = 256;
 
 // One pass in precision R (double or float): the spectrum buffers hold C2<R>::type; the real
@@ -57,19 +57,19 @@ template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_pass(const double* __restrict__ xin, const typename C2<R>::type* __restrict__ cin,
                typename C2<R>::type* cout, double* xout, const FftPass ps, const int dir,
-               const int E, const double2* __restrict__ tw) {
+               const int E, const double2* __restrict__ tw, const int EC) {
   using V = typename C2<R>::type;
   extern __shared__ __align__(16) unsigned char sraw[];
   V* sbuf = reinterpret_cast<V*>(sraw);
   const int line = blockIdx.x;
   const int la = line / ps.B, lb = line % ps.B;
-  const int e0 = blockIdx.y * FFT_EC;
-  const int ec = min(FFT_EC, E - e0);
+  const int e0 = blockIdx.y * EC;
+  const int ec = min(EC, E - e0);
   const int n = ps.n;
   const bool pow2 = (n & (n - 1)) == 0;
   const int logn = 31 - __clz(n);
-  for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
-    const int j = idx / FFT_EC, e = idx % FFT_EC;
+  for (int idx = threadIdx.x; idx < n * EC; idx += FFT_THREADS) {
+    const int j = idx / EC, e = idx % EC;
     if (e >= ec) continue;
     const long slot = ((long)la * n + j) * ps.B + lb;
     V v;
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
       v = cin[slot * E + e0 + e];
     }
     const int jj = (pow2 && n > 1) ? bitrev(j, logn) : j;
-    sbuf[jj * FFT_EC + e] = v;
+    sbuf[jj * EC + e] = v;
   }
   __syncthreads();
   const double2* Wn = tw + ps.w_off;  // exp(-2 pi i t / n)
@@ -89,27 +89,27 @@ __global__ void __launch_bounds__(FFT_THREADS)
   if (pow2) {
     for (int half = 1; half < n; half <<= 1) {
       const int stride = n / (2 * half);
-      for (int idx = threadIdx.x; idx < (n / 2) * FFT_EC; idx += FFT_THREADS) {
-        const int e = idx % FFT_EC, bf = idx / FFT_EC;
+      for (int idx = threadIdx.x; idx < (n / 2) * EC; idx += FFT_THREADS) {
+        const int e = idx % EC, bf = idx / EC;
         const int grp = bf / half, j = bf % half;
         const int i0 = grp * 2 * half + j, i1 = i0 + half;
         const double2 wd = Wn[j * stride];
         const V w = C2<R>::make((R)wd.x, sg * (R)wd.y);
-        const V u = sbuf[i0 * FFT_EC + e];
-        const V t = cmul(w, sbuf[i1 * FFT_EC + e]);
-        sbuf[i0 * FFT_EC + e] = C2<R>::make(u.x + t.x, u.y + t.y);
-        sbuf[i1 * FFT_EC + e] = C2<R>::make(u.x - t.x, u.y - t.y);
+        const V u = sbuf[i0 * EC + e];
+        const V t = cmul(w, sbuf[i1 * EC + e]);
+        sbuf[i0 * EC + e] = C2<R>::make(u.x + t.x, u.y + t.y);
+        sbuf[i1 * EC + e] = C2<R>::make(u.x - t.x, u.y - t.y);
       }
       __syncthreads();
     }
   } else {
-    V* obuf = sbuf + n * FFT_EC;
-    for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
-      const int k = idx / FFT_EC, e = idx % FFT_EC;
+    V* obuf = sbuf + n * EC;
+    for (int idx = threadIdx.x; idx < n * EC; idx += FFT_THREADS) {
+      const int k = idx / EC, e = idx % EC;
       V acc = C2<R>::make(R(0), R(0));
       for (int j = 0; j < n; ++j) {
         const double2 wd = Wn[(j * k) % n];
-        const V t = cmul(C2<R>::make((R)wd.x, sg * (R)wd.y), sbuf[j * FFT_EC + e]);
+        const V t = cmul(C2<R>::make((R)wd.x, sg * (R)wd.y), sbuf[j * EC + e]);
         acc.x += t.x;
         acc.y += t.y;
       }
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
     __syncthreads();
     res = obuf;
   }
-  for (int idx = threadIdx.x; idx < n * FFT_EC; idx += FFT_THREADS) {
-    const int k = idx / FFT_EC, e = idx % FFT_EC;
+  for (int idx = threadIdx.x; idx < n * EC; idx += FFT_THREADS) {
+    const int k = idx / EC, e = idx % EC;
     if (e >= ec) continue;
     V v = res[idx];
     if (ps.tw_mode) {
@@ -209,7 +209,8 @@ __device__ void unpack_block(const V* spec, int s, int s2, int E, T* Ar, T* Ai, 
 template <int D, typename T>
 __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
     k_xproj(typename C2<T>::type* spec, const int* __restrict__ canon, const int ncanon,
-            const FftPlan p, const double invN, T* vstore, const int warm) {
+            const FftPlan p, const double invN, T* vstore, const int warm,
+            unsigned long long* stats) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
   constexpr int GPC = (NT == 32) ? 4 : 1;
   using S = XSmem<D, T>;
@@ -232,6 +233,7 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
     unpack_block<D, NT, LD, T>(spec, s, s2, E, Ar, Ai, tid);
     T* vr = vstore ? vstore + (long)s * 2 * D * D : nullptr;
     T* vi = vr ? vr + D * D : nullptr;
+    int nsw = 0;
     if (warm && vr) {
       // start from the previous eigenvectors: A <- V^H C V
       for (int e = tid; e < D * D; e += NT) {
@@ -269,9 +271,13 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
         }
       }
       gsync<NT>();
-      jacobi_herm<T, D, LD, NT, true, false>(Ar, Ai, Vr, Vi, cs, red, tid);
+      nsw = jacobi_herm<T, D, LD, NT, true, false>(Ar, Ai, Vr, Vi, cs, red, tid);
     } else {
-      jacobi_herm<T, D, LD, NT, true, true>(Ar, Ai, Vr, Vi, cs, red, tid);
+      nsw = jacobi_herm<T, D, LD, NT, true, true>(Ar, Ai, Vr, Vi, cs, red, tid);
+    }
+    if (stats && tid == 0) {
+      atomicAdd(stats, (unsigned long long)nsw);
+      atomicAdd(stats + 1, 1ull);
     }
     if (vr) {
       for (int e = tid; e < D * D; e += NT) {
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
 
 template <int D, typename T>
 cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, void* vstore,
-                           int warm, cudaStream_t s) {
+                           int warm, cudaStream_t s, unsigned long long* stats) {
   constexpr int NT = GroupShape<D>::NT, GPC = (NT == 32) ? 4 : 1;
   const size_t smem = XSmem<D, T>::bytes * GPC;
   static unsigned long long mask = 0;
@@ -384,7 +390,7 @@ cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, vo
   if (blocks > res) blocks = res;
   k_xproj<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(
       reinterpret_cast<typename C2<T>::type*>(spec), canon, nc, p, 1.0 / p.N,
-      reinterpret_cast<T*>(vstore), warm);
+      reinterpret_cast<T*>(vstore), warm, stats);
   return cudaGetLastError();
 }
 
@@ -410,13 +416,18 @@ cudaError_t run_pass_t(const FftPlan& p, const FftPass& ps, int dir, const doubl
                        cudaStream_t s) {
   using V = typename C2<R>::type;
   const bool pow2 = (ps.n & (ps.n - 1)) == 0;
-  const size_t smem = sizeof(V) * ps.n * FFT_EC * (pow2 ? 1 : 2);
+  // narrower entry chunks when the pass has few lines, so that the grid fills the GPU
+  const long lines = (long)ps.A * ps.B;
+  int ec = FFT_EC;
+  while (ec > 8 && lines * ((p.E + ec - 1) / ec) < 304) ec /= 2;
+  const size_t smem = sizeof(V) * ps.n * ec * (pow2 ? 1 : 2);
   static unsigned long long mask = 0;
   cudaError_t e = smem_once(k_fft_pass<R>, 2 * sizeof(V) * 64 * FFT_EC, mask);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(ps.A * ps.B), (unsigned)((p.E + FFT_EC - 1) / FFT_EC));
+  dim3 grid((unsigned)lines, (unsigned)((p.E + ec - 1) / ec));
   k_fft_pass<R><<<grid, FFT_THREADS, smem, s>>>(xin, reinterpret_cast<const V*>(cin),
-                                                reinterpret_cast<V*>(cout), xout, ps, dir, p.E, tw);
+                                                reinterpret_cast<V*>(cout), xout, ps, dir, p.E, tw,
+                                                ec);
   return cudaGetLastError();
 }
 
@@ -428,7 +439,8 @@ cudaError_t run_pass(const FftPlan& p, const FftPass& ps, int dir, const double*
 }
 
 int smallest_factor_pair(int N, int& N1, int& N2) {
-  // N = N1 * N2 with N1 >= N2, both <= 64, preferring the most balanced split
+  // N = N1 * N2 with N1 >= N2, both <= 64, preferring the most balanced split (N2 = 1 when
+  // N <= 64 is prime)
   int best = -1;
   for (int a = 1; a <= 64; ++a) {
     if (N % a) continue;
@@ -454,7 +466,10 @@ int fft_plan_build(FftPlan& p, int dim, const int M[2], int D) {
     p.M1 = 1;
     p.N = M[0];
     if (p.N < 2) return VE_EINVAL;
-    if (p.N <= 64) {
+    int f1 = 0, f2 = 0;
+    const bool pow2 = (p.N & (p.N - 1)) == 0;
+    const bool split = p.N > 64 || (!pow2 && smallest_factor_pair(p.N, f1, f2) == 0 && f2 > 1);
+    if (!split) {
       p.npass = 1;
       p.N1 = p.N;
       p.N2 = 1;
@@ -466,7 +481,7 @@ int fft_plan_build(FftPlan& p, int dim, const int M[2], int D) {
       p.inv[0] = p.fwd[0];
     } else {
       int N1, N2;
-      if (p.N > 4096 || smallest_factor_pair(p.N, N1, N2)) return VE_EUNSUPPORTED;
+      if (p.N > 4096 || smallest_factor_pair(p.N, N1, N2) || N2 < 2) return VE_EUNSUPPORTED;
       p.npass = 2;
       p.N1 = N1;
       p.N2 = N2;
@@ -539,14 +554,14 @@ cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2*
 }
 
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
-                         void* vstore, int warm, cudaStream_t s) {
+                         void* vstore, int warm, cudaStream_t s, unsigned long long* stats) {
   switch (p.D) {
-    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, canon, vstore, warm, s)
-                        : launch_xproj_t<4, double>(p, spec, canon, vstore, warm, s);
-    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, canon, vstore, warm, s)
-                         : launch_xproj_t<16, double>(p, spec, canon, vstore, warm, s);
-    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, canon, vstore, warm, s)
-                         : launch_xproj_t<64, double>(p, spec, canon, vstore, warm, s);
+    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, canon, vstore, warm, s, stats)
+                        : launch_xproj_t<4, double>(p, spec, canon, vstore, warm, s, stats);
+    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, canon, vstore, warm, s, stats)
+                         : launch_xproj_t<16, double>(p, spec, canon, vstore, warm, s, stats);
+    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, canon, vstore, warm, s, stats)
+                         : launch_xproj_t<64, double>(p, spec, canon, vstore, warm, s, stats);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -38,6 +38,7 @@ struct PairArgs {
   double* part;         // P*2     ||rho - rho~||^2, Tr[H rho]
   void* vstore;         // P*D*D eigenvectors of the last projection (float or double)
   int warm;             // 1: start each Jacobi from V^T C V with the stored V
+  unsigned long long* stats;  // null, or [0] += Jacobi sweeps, [1] += matrices (profiling)
 };
 
 struct DevStatus {
@@ -111,7 +112,8 @@ int fft_ncanon(const FftPlan& p);
 // float32 eigensolve.  vstore (N * 2 * D*D of float or double, or null): eigenvectors kept per
 // slot; warm = 1 starts from them.
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
-                         void* vstore, int warm, cudaStream_t s);
+                         void* vstore, int warm, cudaStream_t s,
+                         unsigned long long* stats = nullptr);
 // lmin[slot] = smallest eigenvalue of the (unnormalised) block C_k, +inf for non-canonical slots.
 cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
                        cudaStream_t s);

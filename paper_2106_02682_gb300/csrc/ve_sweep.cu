@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
     }
     gsync<NT>();
     T* vs = reinterpret_cast<T*>(a.vstore) + p * D * D;
+    int nsw = 0;
     if (a.warm) {
       // start from the previous eigenvectors: A <- V^T C V
       for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = vs[e];
@@ -154,9 +155,13 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
         }
       }
       gsync<NT>();
-      jacobi_sym<T, D, LD, NT, true, false>(A, V, cs, red, tid);
+      nsw = jacobi_sym<T, D, LD, NT, true, false>(A, V, cs, red, tid);
     } else {
-      jacobi_sym<T, D, LD, NT, true, true>(A, V, cs, red, tid);
+      nsw = jacobi_sym<T, D, LD, NT, true, true>(A, V, cs, red, tid);
+    }
+    if (a.stats && tid == 0) {
+      atomicAdd(a.stats, (unsigned long long)nsw);
+      atomicAdd(a.stats + 1, 1ull);
     }
     for (int e = tid; e < D * D; e += NT) vs[e] = V[(e / D) * LD + (e % D)];
     for (int k = tid; k < D; k += NT) {

@@ -98,6 +98,7 @@ def _load():
         "ve_error_string": (ctypes.c_char_p, [c_int]),
         "ve_profile": (c_int, [H, c_int]),
         "ve_profile_read": (c_int, [H, P_double, ctypes.POINTER(c_long)]),
+        "ve_profile_sweeps": (c_int, [H, P_double, P_double]),
         "ve_project_psd_sym": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
         "ve_project_psd_herm": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
         "ve_circulant_workspace_size": (c_size_t, [c_int, ctypes.POINTER(c_int), c_int]),
@@ -235,6 +236,13 @@ def ve_profile_read(h):
     n = (c_long * VE_NSTAGE)()
     _check(_lib.ve_profile_read(c_void_p(h), ms, n), "ve_profile_read")
     return {STAGES[i]: (ms[i], n[i]) for i in range(VE_NSTAGE)}
+
+
+def ve_profile_sweeps(h):
+    a, b = c_double(), c_double()
+    _check(_lib.ve_profile_sweeps(c_void_p(h), ctypes.byref(a), ctypes.byref(b)),
+           "ve_profile_sweeps")
+    return a.value, b.value
 
 
 def ve_project_psd_sym(in_ptr, out_ptr, n, count, precision=VE_PREC_FP64, stream=None):

@@ -103,7 +103,8 @@ def test_projection_degenerate_cases(ve):
 
 # ------------------------------------------------------------------ S7-S9: the X step
 
-CIRC = [((2,), 4), ((3,), 16), ((5,), 4), ((16,), 16), ((64,), 16), ((100,), 4), ((96,), 16),
+CIRC = [((2,), 4), ((3,), 16), ((5,), 4), ((6,), 16), ((16,), 16), ((50,), 16), ((64,), 16),
+        ((100,), 4), ((96,), 16),
         ((2048,), 16), ((4096,), 4), ((2, 3), 16), ((4, 4), 4), ((8, 6), 16), ((32, 32), 16),
         ((3,), 64), ((2, 2), 64)]
 
