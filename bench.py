@@ -143,6 +143,19 @@ def ncu_traffic(kernel, workload, precision):
     return rec.get("dram_bytes_per_launch")
 
 
+# ------------------------------------------------------------------ replica aggregation
+def job_rate(local_ms, steps, world, device="cpu"):
+    """Whole-job sweeps per second for `world` replicas: every rank ran `steps` sweeps, the
+    job took as long as the slowest rank (max over ranks of the local device time)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return world * steps / (max_ms / 1e3), max_ms
+
+
 # ------------------------------------------------------------------ CPU oracle timing
 def oracle_rate(workload, seconds, max_sweeps=None):
     import numpy as np  # noqa: F401
@@ -253,12 +266,9 @@ def run_ours(args):
         prof = ve.ve_profile_read(h)
         jac_pair, jac_k = ve.ve_profile_sweeps(h)
         ve.ve_profile(h, 0)
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        value, max_ms = job_rate(total_ms, args.steps, world, device="cuda")
         if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             torch.distributed.barrier()
-        max_ms = float(t.item())
-        value = world * args.steps / (max_ms / 1e3)
         status = ve.ve_get_status(h)
 
         # ---- end to end through the public API with host buffers
