@@ -111,8 +111,10 @@ int ve_ham_xxz(int dim, double J, double delta, ve_hamiltonian* out);
 
 /* Build the cluster blocks H_0, H_{0,delta} (Sec. 2.3, 3.3), allocate the device state and
  * initialise it as in Sec. 4 (Lambda = 0, rho_0 = I/m, rho~ = I/D, X = I).
- * Supported: L = spins per cluster in {1, 2, 3}; clusters per axis M_p >= 1 with N >= 2; 1-D
- * lattices with N <= 4096 factoring as N1*N2, N1, N2 <= 64; 2-D lattices with M_p <= 64.
+ * Supported: L = spins per cluster in {1, 2, 3, 4} (D = 4, 16, 64, 256); clusters per axis
+ * M_p >= 1 with N >= 2; 1-D lattices with N <= 64, or N <= 4096 factoring as N1*N2 with
+ * N1, N2 <= 64; 2-D lattices with M_p <= 64.  With L = 4 the eigensolves stage their 256 x 256
+ * matrices in a device workspace of ~3.2 MB per SM.
  * opt may be NULL (defaults).  On success *out owns all device memory until ve_destroy.
  * Errors: VE_EINVAL (bad shape, cluster does not tile the lattice, N < 2, bad options),
  * VE_EUNSUPPORTED (sizes outside the list above), VE_ENOMEM, VE_ECUDA. */
@@ -186,7 +188,9 @@ int ve_project_psd_herm(const double* in, double* out, int n, long count, int pr
  * X'_{0,-delta} = X'_{0,delta}^T (then every C_k is Hermitian); it may alias the output.
  * workspace: device buffer of at least ve_circulant_workspace_size(...) bytes, 256-byte
  * aligned.  D in {4, 16, 64}.  Asynchronous on `stream`.  Errors: VE_EINVAL (sizes, NULL,
- * small workspace), VE_EUNSUPPORTED (lattice not factorable as for ve_create), VE_ECUDA. */
+ * small workspace), VE_EUNSUPPORTED (lattice not factorable as for ve_create, or D = 256,
+ * which only a handle serves), VE_ECUDA.  ve_circulant_workspace_size returns 0 for unsupported
+ * shapes. */
 size_t ve_circulant_workspace_size(int dim, const int M[2], int D);
 int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M[2], int D,
                          int precision, void* workspace, size_t workspace_bytes, void* stream);

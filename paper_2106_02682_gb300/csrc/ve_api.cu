@@ -77,7 +77,7 @@ int build_model(const ve_lattice* lat, const ve_cluster* clu, const ve_hamiltoni
   md.N = md.M0 * md.M1;
   md.L = md.c0 * md.c1;
   if (md.N < 2) return VE_EINVAL;
-  if (md.L < 1 || md.L > 3) return VE_EUNSUPPORTED;
+  if (md.L < 1 || md.L > 4) return VE_EUNSUPPORTED;
   if (ham->nbond < 0 || ham->nbond > VE_MAX_BONDS) return VE_EINVAL;
   md.m = 1 << md.L;
   md.D = md.m * md.m;
@@ -166,6 +166,7 @@ struct ve_handle {
   cudaEvent_t ev[VE_NSTAGE + 1] = {};
   double prof_ms[VE_NSTAGE] = {};
   unsigned long long* jstats = nullptr;  // device: pair sweeps, pair matrices, k sweeps, k matrices
+  unsigned char* gws = nullptr;          // D = 256: staging workspace of the eigensolver kernels
   long prof_launch[VE_NSTAGE] = {};
   int stage_launches[VE_NSTAGE] = {};
 };
@@ -235,6 +236,7 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
   pa.vstore = h->vpair[v];
   pa.warm = warm ? 1 : 0;
   pa.stats = h->prof ? h->jstats : nullptr;
+  pa.gws = h->gws;
   const SmallArgs sa = small_args(h);
   cudaError_t e;
   auto mark = [&](int i) { return h->prof ? cudaEventRecord(h->ev[i], s) : cudaSuccess; };
@@ -252,7 +254,7 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
     return e;
   if ((e = mark(5)) != cudaSuccess) return e;
   if ((e = launch_xproj(h->plan, spec, h->canon, fp32, h->vk[v], warm ? 1 : 0, s,
-                       h->prof ? h->jstats + 2 : nullptr)) != cudaSuccess)
+                       h->prof ? h->jstats + 2 : nullptr, h->gws)) != cudaSuccess)
     return e;
   if ((e = mark(6)) != cudaSuccess) return e;
   if ((e = fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, fp32, s)) != cudaSuccess)
@@ -465,6 +467,10 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   const size_t o_tw = take(sizeof(double2) * h->plan.ntw);
   const size_t o_st = take(sizeof(DevStatus));
   const size_t o_js = take(sizeof(unsigned long long) * 4);
+  size_t gws_bytes = pair_ws_bytes(D);
+  if (xproj_ws_bytes(D) > gws_bytes) gws_bytes = xproj_ws_bytes(D);
+  if (bound_ws_bytes(D) > gws_bytes) gws_bytes = bound_ws_bytes(D);
+  const size_t o_gws = take(gws_bytes > 0 ? gws_bytes : 1);
   if (cudaMalloc(&h->dev, off) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -507,6 +513,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   h->tw = (double2*)(base + o_tw);
   h->dst = (DevStatus*)(base + o_st);
   h->jstats = (unsigned long long*)(base + o_js);
+  h->gws = gws_bytes > 0 ? (unsigned char*)(base + o_gws) : nullptr;
   if (h->opt.stream) {
     h->stream = (cudaStream_t)h->opt.stream;
   } else {
@@ -708,7 +715,7 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   const int N = md.N, P = h->P;
   double2* spec = nullptr;
   VE_CU(fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, false, h->stream));
-  VE_CU(launch_xeig(h->plan, spec, h->canon, h->lmin_k, h->stream));
+  VE_CU(launch_xeig(h->plan, spec, h->canon, h->lmin_k, h->stream, h->gws));
   BoundArgs b;
   b.N = N;
   b.P = P;
@@ -722,6 +729,7 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   b.H0 = h->H0;
   b.lmin_pairs = h->lmin_pairs;
   b.lmin0 = h->lmin0;
+  b.gws = h->gws;
   VE_CU(launch_bound(b, h->stream));
   std::vector<double> lp(P), lk(h->ncanon);
   double l0 = 0;
@@ -765,7 +773,7 @@ int ve_project_psd_herm(const double* in, double* out, int n, long count, int pr
 }
 
 size_t ve_circulant_workspace_size(int dim, const int M[2], int D) {
-  if (!M) return 0;
+  if (!M || D == 256) return 0;
   FftPlan p;
   if (fft_plan_build(p, dim, M, D) != 0) return 0;
   return align_up(sizeof(double2) * (size_t)p.N * p.E) * 2 + align_up(sizeof(double2) * p.ntw) +
@@ -777,6 +785,7 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
   if (!x_in || !x_out || !M || !workspace) return VE_EINVAL;
   if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
   if (((uintptr_t)workspace) % kAlign) return VE_EINVAL;
+  if (D == 256) return VE_EUNSUPPORTED;
   FftPlan p;
   const int rc = fft_plan_build(p, dim, M, D);
   if (rc != 0) return rc;

@@ -19,11 +19,11 @@ namespace {
 
 template <int D>
 struct BShape {
-  static constexpr int m = (D == 4) ? 2 : (D == 16) ? 4 : 8;
+  static constexpr int m = ClusterDim<D>::m;
   static constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
-  static constexpr int GPC = (NT == 32) ? 4 : 1;
-  static constexpr size_t MAT = sizeof(double) * D * LD;
-  static constexpr size_t bytes = MAT + sizeof(double) * D * D + sizeof(double) * (D + 16);
+  static constexpr int GPC = GroupShape<D>::GPC;
+  static constexpr size_t MAT = ((sizeof(double) * D * LD + 15) / 16) * 16;
+  static constexpr size_t bytes = MAT + sizeof(double) * D * D + sizeof(double) * (D + 32);
 };
 
 template <int D>
@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(BShape<D>::NT * BShape<D>::GPC) k_bound_pairs(
   constexpr int m = BShape<D>::m, NT = BShape<D>::NT, LD = BShape<D>::LD, GPC = BShape<D>::GPC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
-  unsigned char* base = smem_raw + (size_t)g * BShape<D>::bytes;
+  unsigned char* base = GroupShape<D>::GLOBAL ? a.gws + (size_t)blockIdx.x * BShape<D>::bytes
+                                              : smem_raw + (size_t)g * BShape<D>::bytes;
   double* A = reinterpret_cast<double*>(base);
   double* Xs = reinterpret_cast<double*>(base + BShape<D>::MAT);
   double* cs = Xs + D * D;
@@ -226,12 +227,19 @@ __global__ void __launch_bounds__(PShape<n, T>::NT * PShape<n, T>::GPC)
 template <int D>
 cudaError_t launch_bound_t(const BoundArgs& a, cudaStream_t s) {
   constexpr int NT = BShape<D>::NT, GPC = BShape<D>::GPC, m = BShape<D>::m;
-  const size_t smem = BShape<D>::bytes * GPC;
-  static unsigned long long mask = 0;
-  cudaError_t e = smem_once(k_bound_pairs<D>, smem, mask);
-  if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((a.P + GPC - 1) / GPC);
-  k_bound_pairs<D><<<blocks, NT * GPC, smem, s>>>(a);
+  constexpr bool G = GroupShape<D>::GLOBAL;
+  const size_t smem = G ? 0 : BShape<D>::bytes * GPC;
+  cudaError_t e = cudaSuccess;
+  if (!G) {
+    static unsigned long long mask = 0;
+    e = smem_once(k_bound_pairs<D>, smem, mask);
+    if (e != cudaSuccess) return e;
+  } else if (!a.gws) {
+    return cudaErrorInvalidValue;
+  }
+  long blocks = (a.P + GPC - 1) / GPC;
+  if (G && blocks > big_grid()) blocks = big_grid();
+  k_bound_pairs<D><<<(unsigned)blocks, NT * GPC, smem, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_bound_k0<m><<<1, 256, 0, s>>>(a);
@@ -271,9 +279,12 @@ cudaError_t launch_bound(const BoundArgs& a, cudaStream_t s) {
     case 4: return launch_bound_t<4>(a, s);
     case 16: return launch_bound_t<16>(a, s);
     case 64: return launch_bound_t<64>(a, s);
+    case 256: return launch_bound_t<256>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
+
+size_t bound_ws_bytes(int D) { return D == 256 ? BShape<256>::bytes * (size_t)big_grid() : 0; }
 
 cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, bool fp32,
                             cudaStream_t s) {

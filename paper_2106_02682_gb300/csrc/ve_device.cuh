@@ -398,11 +398,22 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
   return sweep;
 }
 
-// Threads per group and leading dimension used for an n x n matrix.
+// Threads per group, leading dimension and staging of an n x n matrix.  n <= 16: one warp;
+// n = 64: one CTA of 256 threads; n = 256: one CTA of 512 threads whose matrices are staged in a
+// per-CTA slice of a global workspace (1 MB per float64 matrix and its eigenvectors does not fit
+// in shared memory), one CTA per SM so that the slices stay L2-resident where they fit.
 template <int n>
 struct GroupShape {
-  static constexpr int NT = (n <= 16) ? 32 : 256;
+  static constexpr int NT = (n <= 16) ? 32 : (n <= 64 ? 256 : 512);
   static constexpr int LD = n + 1;
+  static constexpr bool GLOBAL = n > 64;
+  static constexpr int GPC = (NT == 32) ? 4 : 1;  // groups per CTA
+};
+
+// m = sqrt(D) for the pair dimension D = m^2 of a cluster of dimension m.
+template <int D>
+struct ClusterDim {
+  static constexpr int m = (D == 4) ? 2 : (D == 16) ? 4 : (D == 64) ? 8 : 16;
 };
 
 }  // namespace ve

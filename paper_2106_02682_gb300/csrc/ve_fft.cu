@@ -166,7 +166,7 @@ struct XSmem {
   static constexpr int LD = GroupShape<D>::LD;
   static constexpr size_t MAT = ((sizeof(T) * D * LD + 15) / 16) * 16;
   static constexpr size_t bytes = 6 * MAT + ((sizeof(T) * 2 * D + 15) / 16) * 16 +
-                                  ((sizeof(T) * D + 15) / 16) * 16 + 16 * sizeof(T);
+                                  ((sizeof(T) * D + 15) / 16) * 16 + 32 * sizeof(T);
 };
 
 // Unpack block C_k (unnormalised) of slot s from the packed spectrum into (Ar, Ai), Hermitised.
@@ -207,16 +207,17 @@ __device__ void unpack_block(const V* spec, int s, int s2, int E, T* Ar, T* Ai, 
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
+__global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
     k_xproj(typename C2<T>::type* spec, const int* __restrict__ canon, const int ncanon,
             const FftPlan p, const double invN, T* vstore, const int warm,
-            unsigned long long* stats) {
+            unsigned long long* stats, unsigned char* gws) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
-  constexpr int GPC = (NT == 32) ? 4 : 1;
+  constexpr int GPC = GroupShape<D>::GPC;
   using S = XSmem<D, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
-  unsigned char* base = smem_raw + (size_t)g * S::bytes;
+  unsigned char* base = GroupShape<D>::GLOBAL ? gws + (size_t)blockIdx.x * S::bytes
+                                              : smem_raw + (size_t)g * S::bytes;
   T* Ar = reinterpret_cast<T*>(base);
   T* Ai = reinterpret_cast<T*>(base + S::MAT);
   T* Vr = reinterpret_cast<T*>(base + 2 * S::MAT);
@@ -349,15 +350,16 @@ __global__ void __launch_bounds__(256) k_canon_list(const FftPlan p, int* canon)
 }
 
 template <int D>
-__global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32) ? 4 : 1))
+__global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
     k_xeig(const double2* spec, const int* __restrict__ canon, const int ncanon, const FftPlan p,
-           double* lmin) {
+           double* lmin, unsigned char* gws) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
-  constexpr int GPC = (NT == 32) ? 4 : 1;
+  constexpr int GPC = GroupShape<D>::GPC;
   using S = XSmem<D, double>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
-  unsigned char* base = smem_raw + (size_t)g * S::bytes;
+  unsigned char* base = GroupShape<D>::GLOBAL ? gws + (size_t)blockIdx.x * S::bytes
+                                              : smem_raw + (size_t)g * S::bytes;
   double* Ar = reinterpret_cast<double*>(base);
   double* Ai = reinterpret_cast<double*>(base + S::MAT);
   double* cs = reinterpret_cast<double*>(base + 4 * S::MAT);
@@ -378,35 +380,46 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * ((GroupShape<D>::NT == 32)
 
 template <int D, typename T>
 cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, void* vstore,
-                           int warm, cudaStream_t s, unsigned long long* stats) {
-  constexpr int NT = GroupShape<D>::NT, GPC = (NT == 32) ? 4 : 1;
-  const size_t smem = XSmem<D, T>::bytes * GPC;
-  static unsigned long long mask = 0;
-  cudaError_t e = smem_once(k_xproj<D, T>, smem, mask);
-  if (e != cudaSuccess) return e;
+                           int warm, cudaStream_t s, unsigned long long* stats,
+                           unsigned char* gws) {
+  constexpr int NT = GroupShape<D>::NT, GPC = GroupShape<D>::GPC;
+  constexpr bool G = GroupShape<D>::GLOBAL;
+  const size_t smem = G ? 0 : XSmem<D, T>::bytes * GPC;
+  if (!G) {
+    static unsigned long long mask = 0;
+    cudaError_t e = smem_once(k_xproj<D, T>, smem, mask);
+    if (e != cudaSuccess) return e;
+  } else if (!gws) {
+    return cudaErrorInvalidValue;
+  }
   const int nc = fft_ncanon(p);
   long blocks = (nc + GPC - 1) / GPC;
-  const long res = resident_grid((const void*)k_xproj<D, T>, NT * GPC, smem);
+  const long res = G ? (long)big_grid() : resident_grid((const void*)k_xproj<D, T>, NT * GPC, smem);
   if (blocks > res) blocks = res;
   k_xproj<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(
       reinterpret_cast<typename C2<T>::type*>(spec), canon, nc, p, 1.0 / p.N,
-      reinterpret_cast<T*>(vstore), warm, stats);
+      reinterpret_cast<T*>(vstore), warm, stats, gws);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_xeig_t(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
-                          cudaStream_t s) {
-  constexpr int NT = GroupShape<D>::NT, GPC = (NT == 32) ? 4 : 1;
-  const size_t smem = XSmem<D, double>::bytes * GPC;
-  static unsigned long long mask = 0;
-  cudaError_t e = smem_once(k_xeig<D>, smem, mask);
-  if (e != cudaSuccess) return e;
+                          cudaStream_t s, unsigned char* gws) {
+  constexpr int NT = GroupShape<D>::NT, GPC = GroupShape<D>::GPC;
+  constexpr bool G = GroupShape<D>::GLOBAL;
+  const size_t smem = G ? 0 : XSmem<D, double>::bytes * GPC;
+  if (!G) {
+    static unsigned long long mask = 0;
+    cudaError_t e = smem_once(k_xeig<D>, smem, mask);
+    if (e != cudaSuccess) return e;
+  } else if (!gws) {
+    return cudaErrorInvalidValue;
+  }
   const int nc = fft_ncanon(p);
   long blocks = (nc + GPC - 1) / GPC;
-  const long res = resident_grid((const void*)k_xeig<D>, NT * GPC, smem);
+  const long res = G ? (long)big_grid() : resident_grid((const void*)k_xeig<D>, NT * GPC, smem);
   if (blocks > res) blocks = res;
-  k_xeig<D><<<(unsigned)blocks, NT * GPC, smem, s>>>(spec, canon, nc, p, lmin);
+  k_xeig<D><<<(unsigned)blocks, NT * GPC, smem, s>>>(spec, canon, nc, p, lmin, gws);
   return cudaGetLastError();
 }
 
@@ -522,7 +535,7 @@ int fft_plan_build(FftPlan& p, int dim, const int M[2], int D) {
   } else {
     return VE_EINVAL;
   }
-  if (D != 4 && D != 16 && D != 64) return VE_EUNSUPPORTED;
+  if (D != 4 && D != 16 && D != 64 && D != 256) return VE_EUNSUPPORTED;
   return 0;
 }
 
@@ -554,26 +567,36 @@ cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2*
 }
 
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
-                         void* vstore, int warm, cudaStream_t s, unsigned long long* stats) {
+                         void* vstore, int warm, cudaStream_t s, unsigned long long* stats,
+                         unsigned char* gws) {
   switch (p.D) {
-    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, canon, vstore, warm, s, stats)
-                        : launch_xproj_t<4, double>(p, spec, canon, vstore, warm, s, stats);
-    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, canon, vstore, warm, s, stats)
-                         : launch_xproj_t<16, double>(p, spec, canon, vstore, warm, s, stats);
-    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, canon, vstore, warm, s, stats)
-                         : launch_xproj_t<64, double>(p, spec, canon, vstore, warm, s, stats);
+    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, canon, vstore, warm, s, stats, gws)
+                        : launch_xproj_t<4, double>(p, spec, canon, vstore, warm, s, stats, gws);
+    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, canon, vstore, warm, s, stats, gws)
+                         : launch_xproj_t<16, double>(p, spec, canon, vstore, warm, s, stats, gws);
+    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, canon, vstore, warm, s, stats, gws)
+                         : launch_xproj_t<64, double>(p, spec, canon, vstore, warm, s, stats, gws);
+    case 256: return fp32 ? launch_xproj_t<256, float>(p, spec, canon, vstore, warm, s, stats, gws)
+                          : launch_xproj_t<256, double>(p, spec, canon, vstore, warm, s, stats, gws);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
-                        cudaStream_t s) {
+                        cudaStream_t s, unsigned char* gws) {
   switch (p.D) {
-    case 4: return launch_xeig_t<4>(p, spec, canon, lmin, s);
-    case 16: return launch_xeig_t<16>(p, spec, canon, lmin, s);
-    case 64: return launch_xeig_t<64>(p, spec, canon, lmin, s);
+    case 4: return launch_xeig_t<4>(p, spec, canon, lmin, s, gws);
+    case 16: return launch_xeig_t<16>(p, spec, canon, lmin, s, gws);
+    case 64: return launch_xeig_t<64>(p, spec, canon, lmin, s, gws);
+    case 256: return launch_xeig_t<256>(p, spec, canon, lmin, s, gws);
     default: return cudaErrorInvalidValue;
   }
+}
+
+size_t xproj_ws_bytes(int D) {
+  if (D != 256) return 0;
+  const size_t a = XSmem<256, double>::bytes, b = XSmem<256, float>::bytes;
+  return (a > b ? a : b) * (size_t)big_grid();
 }
 
 cudaError_t launch_canon_list(const FftPlan& p, int* canon, cudaStream_t s) {

@@ -39,6 +39,7 @@ struct PairArgs {
   void* vstore;         // P*D*D eigenvectors of the last projection (float or double)
   int warm;             // 1: start each Jacobi from V^T C V with the stored V
   unsigned long long* stats;  // null, or [0] += Jacobi sweeps, [1] += matrices (profiling)
+  unsigned char* gws;   // D = 256: per-CTA staging workspace (pair_ws_bytes), else unused
 };
 
 struct DevStatus {
@@ -67,6 +68,12 @@ struct SmallArgs {
 
 // Number of CTAs that keep every SM busy for a kernel with the given block shape.
 int resident_grid(const void* kernel, int threads, size_t smem);
+// D = 256 kernels run one CTA per SM with their matrices in a global workspace; these give the
+// grid and the workspace bytes each kernel family needs (0 for D <= 64).
+int big_grid();
+size_t pair_ws_bytes(int D);
+size_t xproj_ws_bytes(int D);
+size_t bound_ws_bytes(int D);
 
 // D in {4, 16, 64}; fp32 selects the float32 projection.
 cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s);
@@ -113,10 +120,10 @@ int fft_ncanon(const FftPlan& p);
 // slot; warm = 1 starts from them.
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
                          void* vstore, int warm, cudaStream_t s,
-                         unsigned long long* stats = nullptr);
+                         unsigned long long* stats = nullptr, unsigned char* gws = nullptr);
 // lmin[slot] = smallest eigenvalue of the (unnormalised) block C_k, +inf for non-canonical slots.
 cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
-                       cudaStream_t s);
+                       cudaStream_t s, unsigned char* gws = nullptr);
 
 // ------------------------------------------------------------------ bound
 struct BoundArgs {
@@ -129,6 +136,7 @@ struct BoundArgs {
   const double* H0;
   double* lmin_pairs;   // P
   double* lmin0;        // 1
+  unsigned char* gws;   // D = 256: per-CTA staging workspace (bound_ws_bytes)
 };
 cudaError_t launch_bound(const BoundArgs& a, cudaStream_t s);
 

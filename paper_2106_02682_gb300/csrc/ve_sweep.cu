@@ -20,10 +20,10 @@ namespace {
 
 template <int D>
 struct PairShape {
-  static constexpr int m = (D == 4) ? 2 : (D == 16) ? 4 : 8;
+  static constexpr int m = ClusterDim<D>::m;
   static constexpr int NT = GroupShape<D>::NT;
   static constexpr int LD = GroupShape<D>::LD;
-  static constexpr int GPC = (NT == 32) ? 4 : 1;  // groups per CTA
+  static constexpr int GPC = GroupShape<D>::GPC;  // groups per CTA
 };
 
 template <int D, typename T>
@@ -40,7 +40,7 @@ struct PairSmem {
   static constexpr size_t W = CS + al(sizeof(T) * D);              // T D
   static constexpr size_t TR = W + al(sizeof(T) * D);              // T 2*m*m + 2
   static constexpr size_t RED = TR + al(sizeof(T) * (2 * m * m + 2));
-  static constexpr size_t bytes = RED + al(sizeof(T) * 8);
+  static constexpr size_t bytes = RED + al(sizeof(T) * 32);
 };
 
 // Arithmetic in T (double, or float in the mixed-precision sweep); the state stays float64.
@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
   using S = PairSmem<D, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
-  unsigned char* base = smem_raw + (size_t)g * S::bytes;
+  unsigned char* base = GroupShape<D>::GLOBAL ? a.gws + (size_t)blockIdx.x * S::bytes
+                                              : smem_raw + (size_t)g * S::bytes;
   T* R = reinterpret_cast<T*>(base + S::R);
   T* Xs = reinterpret_cast<T*>(base + S::Xs);
   T* A = reinterpret_cast<T*>(base + S::A);
@@ -220,12 +221,16 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
 template <int D, typename T>
 cudaError_t launch_pair_t(const PairArgs& a, cudaStream_t s) {
   constexpr int NT = PairShape<D>::NT, GPC = PairShape<D>::GPC;
-  const size_t smem = PairSmem<D, T>::bytes * GPC;
-  static unsigned long long mask = 0;
-  cudaError_t e = smem_once(k_pair<D, T>, smem, mask);
-  if (e != cudaSuccess) return e;
+  constexpr bool G = GroupShape<D>::GLOBAL;
+  const size_t smem = G ? 0 : PairSmem<D, T>::bytes * GPC;
+  cudaError_t e = cudaSuccess;
+  if (!G) {
+    static unsigned long long mask = 0;
+    e = smem_once(k_pair<D, T>, smem, mask);
+    if (e != cudaSuccess) return e;
+  }
   long blocks = (a.P + GPC - 1) / GPC;
-  const long res = resident_grid((const void*)k_pair<D, T>, NT * GPC, smem);
+  const long res = G ? (long)big_grid() : resident_grid((const void*)k_pair<D, T>, NT * GPC, smem);
   if (blocks > res) blocks = res;
   if (blocks < 1) blocks = 1;
   k_pair<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(a);
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(256) k_rho0_partial(const SmallArgs a, double*
 }
 
 __global__ void __launch_bounds__(256) k_rho0(const SmallArgs a, const double* partial) {
-  __shared__ double rp[64];
+  __shared__ double rp[256];
   __shared__ double red[8];
   const int m = a.m, mm = m * m, D = a.D;
   const int t = threadIdx.x;
@@ -362,8 +367,22 @@ cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s) {
     case 4: return fp32 ? launch_pair_t<4, float>(a, s) : launch_pair_t<4, double>(a, s);
     case 16: return fp32 ? launch_pair_t<16, float>(a, s) : launch_pair_t<16, double>(a, s);
     case 64: return fp32 ? launch_pair_t<64, float>(a, s) : launch_pair_t<64, double>(a, s);
+    case 256: return fp32 ? launch_pair_t<256, float>(a, s) : launch_pair_t<256, double>(a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+size_t pair_ws_bytes(int D) {
+  if (D != 256) return 0;
+  const size_t a = PairSmem<256, double>::bytes, b = PairSmem<256, float>::bytes;
+  return (a > b ? a : b) * (size_t)big_grid();
+}
+
+int big_grid() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
 }
 
 cudaError_t launch_rho0(const SmallArgs& a, cudaStream_t s) {

@@ -76,4 +76,9 @@ WORKLOADS = {
     "tfim1d_L1_N16": dict(lattice=(16,), cluster=(1,), h=1.0, kind="tfim"),
     # 2-D square lattice 64 x 64, h = 3, 2 x 1 clusters (16 x 16 pair marginals), 32 x 64 clusters
     "tfim2d_L2_64x64": dict(lattice=(64, 64), cluster=(2, 1), h=3.0, kind="tfim"),
+    # 1-D TFI chain of 4096 spins, h = 1, 4-spin clusters (16 x 16 cluster marginals, 256 x 256
+    # pair marginals), 1024 clusters
+    "tfim1d_L4_N1024": dict(lattice=(4096,), cluster=(4,), h=1.0, kind="tfim"),
+    # 2-D square lattice 64 x 64, h = 3, 2 x 2 clusters (256 x 256 pair marginals), 32 x 32 clusters
+    "tfim2d_L4_32x32": dict(lattice=(64, 64), cluster=(2, 2), h=3.0, kind="tfim"),
 }

@@ -96,7 +96,7 @@ def test_site_terms_match_the_oracle_models(ve, dim):
 @pytest.mark.parametrize("lattice,cluster,code", [
     ((8,), (3,), -1),          # cluster does not tile the lattice
     ((2,), (2,), -1),          # a single cluster (N < 2)
-    ((16,), (4,), -5),         # 4-spin clusters: not built here
+    ((20,), (5,), -5),         # 5-spin clusters (D = 1024): not built here
     ((4 * 67,), (1,), -5),     # N = 268 > 64 does not split into two factors <= 64
     ((8000,), (1,), -5),       # N > 4096
     ((130, 4), (1, 1), -5),    # 2-D axis with more than 64 clusters

@@ -152,6 +152,9 @@ SWEEP_CASES = [
     ((6, 4), (1, 2), "tfim", 3.0),
     ((12,), (3,), "tfim", 1.0),
     ((6, 4), (3, 1), "xxz", 1.0),
+    ((8,), (4,), "tfim", 1.0),
+    ((16,), (4,), "xxz", 0.7),
+    ((4, 4), (2, 2), "tfim", 3.0),
 ]
 
 
@@ -281,11 +284,11 @@ def test_mixed_precision_reaches_the_float64_bound(ve):
     assert max(out.values()) <= mo.tfim_chain_jw_energy(32, 1.0, 1.0) / 32
 
 
-def test_mixed_sweeps_track_the_oracle(ve):
+@pytest.mark.parametrize("lattice,cluster", [((64,), (2,)), ((16,), (4,))])
+def test_mixed_sweeps_track_the_oracle(ve, lattice, cluster):
     """Mixed-precision sweeps (float32 arithmetic in the pair pass, the DFT and both
     projections; float64 state and reductions) stay within float32 rounding of the float64
     oracle: 2e-4 relative on the whole state after 30 sweeps."""
-    lattice, cluster = (64,), (2,)
     pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 0.8, 1)))
     st = vo.initial_state(pb)
     h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 0.8),
