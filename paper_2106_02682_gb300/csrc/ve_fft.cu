@@ -231,17 +231,54 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
   for (int j = blockIdx.x * GPC + g; j < ncanon; j += gridDim.x * GPC) {
     const int s = canon[j];
     const int s2 = partner_slot(p, s);
-    unpack_block<D, NT, LD, T>(spec, s, s2, E, Ar, Ai, tid);
     T* vr = vstore ? vstore + (long)s * 2 * D * D : nullptr;
     T* vi = vr ? vr + D * D : nullptr;
     int nsw = 0;
     if (warm && vr) {
-      // start from the previous eigenvectors: A <- V^H C V
       for (int e = tid; e < D * D; e += NT) {
         Vr[(e / D) * LD + (e % D)] = vr[e];
         Vi[(e / D) * LD + (e % D)] = vi[e];
       }
       gsync<NT>();
+      if constexpr (sizeof(T) == 4) {
+        // one Newton-Schulz step V <- V (3 I - V^H V) / 2 against float32 drift of the
+        // stored eigenvectors (Wr/Wi hold the Gram correction, Ar/Ai the new V)
+        for (int e = tid; e < D * D; e += NT) {
+          const int i = e / D, jj = e % D;
+          T gr = T(0), gi = T(0);
+          for (int k = 0; k < D; ++k) {
+            const T ar = Vr[k * LD + i], ai = -Vi[k * LD + i];
+            const T br = Vr[k * LD + jj], bi = Vi[k * LD + jj];
+            gr += ar * br - ai * bi;
+            gi += ar * bi + ai * br;
+          }
+          Wr[i * LD + jj] = ((i == jj) ? T(1.5) : T(0)) - T(0.5) * gr;
+          Wi[i * LD + jj] = -T(0.5) * gi;
+        }
+        gsync<NT>();
+        for (int e = tid; e < D * D; e += NT) {
+          const int i = e / D, jj = e % D;
+          T xr = T(0), xi = T(0);
+          for (int k = 0; k < D; ++k) {
+            const T ar = Vr[i * LD + k], ai = Vi[i * LD + k];
+            const T br = Wr[k * LD + jj], bi = Wi[k * LD + jj];
+            xr += ar * br - ai * bi;
+            xi += ar * bi + ai * br;
+          }
+          Ar[i * LD + jj] = xr;
+          Ai[i * LD + jj] = xi;
+        }
+        gsync<NT>();
+        for (int e = tid; e < D * D; e += NT) {
+          Vr[(e / D) * LD + (e % D)] = Ar[(e / D) * LD + (e % D)];
+          Vi[(e / D) * LD + (e % D)] = Ai[(e / D) * LD + (e % D)];
+        }
+        gsync<NT>();
+      }
+    }
+    unpack_block<D, NT, LD, T>(spec, s, s2, E, Ar, Ai, tid);
+    if (warm && vr) {
+      // start from the previous eigenvectors: A <- V^H C V
       for (int e = tid; e < D * D; e += NT) {  // W = C V
         const int i = e / D, jj = e % D;
         T xr = T(0), xi = T(0);

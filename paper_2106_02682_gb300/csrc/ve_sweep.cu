@@ -120,6 +120,32 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
       R[e] = (y - P1 - P2 + Q) * c0 + (P1 + P2 - T(2) * Q) * c1 + Q * c2;
     }
     gsync<NT>();
+    T* vs = reinterpret_cast<T*>(a.vstore) + p * D * D;
+    int nsw = 0;
+    if (a.warm) {
+      for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = vs[e];
+      gsync<NT>();
+      if constexpr (sizeof(T) == 4) {
+        // float32 rotations erode V's orthogonality over many sweeps; one Newton-Schulz step
+        // V <- V (3 I - V^T V) / 2 squares the error before V is used (A and Wt as scratch)
+        for (int e = tid; e < D * D; e += NT) {
+          const int i = e / D, j = e % D;
+          T acc = T(0);
+          for (int k = 0; k < D; ++k) acc += V[k * LD + i] * V[k * LD + j];
+          Wt[i * LD + j] = ((i == j) ? T(1.5) : T(0)) - T(0.5) * acc;
+        }
+        gsync<NT>();
+        for (int e = tid; e < D * D; e += NT) {
+          const int i = e / D, j = e % D;
+          T acc = T(0);
+          for (int k = 0; k < D; ++k) acc += V[i * LD + k] * Wt[k * LD + j];
+          A[i * LD + j] = acc;
+        }
+        gsync<NT>();
+        for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = A[(e / D) * LD + (e % D)];
+        gsync<NT>();
+      }
+    }
     // C = rho - Lambda / mu, symmetrised, into A
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
@@ -131,12 +157,8 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
       }
     }
     gsync<NT>();
-    T* vs = reinterpret_cast<T*>(a.vstore) + p * D * D;
-    int nsw = 0;
     if (a.warm) {
       // start from the previous eigenvectors: A <- V^T C V
-      for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = vs[e];
-      gsync<NT>();
       for (int e = tid; e < D * D; e += NT) {
         const int i = e / D, j = e % D;
         T acc = T(0);
