@@ -3,7 +3,9 @@ element, on the same seeded inputs.
 
 Tolerances (float64 mode): 1e-10 relative to the largest entry of the compared array, the
 target for float64 results; both sides run the same float64 arithmetic in a different order
-(Jacobi vs LAPACK eigensolver, FFT vs numpy FFT), so agreement is ~1e-13 in practice.  Float32
+(Jacobi vs LAPACK eigensolver, FFT vs numpy FFT), so agreement is ~1e-13 in practice for
+D <= 64.  The eigensolvers' backward error grows like D eps ||A||, so scalar results (energy,
+bound) of multi-sweep runs at D = 256 are held to 1e-10 * D / 64.  Float32
 projections (VE_PREC_MIXED) are held to 8 (n + 16) 2^-24 ||A||_2 per entry: a float32 Jacobi
 eigensolve of an n x n matrix runs ~10 sweeps of n - 1 rounds, and the measured error is
 (20 + 1.3 n) 2^-24 ||A||_2 at n = 4 .. 64, so this keeps a ~4x margin.  The final certified
@@ -22,6 +24,11 @@ torch = pytest.importorskip("torch")
 
 RTOL64 = 1e-10
 RTOL32 = 2e-5    # relative tolerance of float32 results on O(1) arrays (X step, 16 x 16 blocks)
+
+
+def rtol64(D):
+    """float64 tolerance of scalar results for pair dimension D."""
+    return RTOL64 * max(1.0, D / 64.0)
 
 
 def tol32(A):
@@ -184,14 +191,15 @@ def test_sweeps_match_oracle(ve, lattice, cluster, kind, x):
             assert code == 0 and status.iter == done
             err = relerr(ve.ve_get_state(h), vo.pack_state(pb, st))
             assert err < RTOL64, (done, err)
-            assert abs(status.energy_per_spin - diag['energy']) < RTOL64
-            assert abs(status.feas_err - diag['feas_err']) < RTOL64 * max(1.0, diag['feas_err'])
+            tol = rtol64(pb.D)
+            assert abs(status.energy_per_spin - diag['energy']) < tol
+            assert abs(status.feas_err - diag['feas_err']) < tol * max(1.0, diag['feas_err'])
             if done > 1:
-                assert abs(status.d_energy - diag['d_energy']) < RTOL64
+                assert abs(status.d_energy - diag['d_energy']) < tol
         cert = ve.ve_bound(h)
         ocert = vo.certified_bound(pb, st)
         for key in ('bound_per_spin', 'raw_bound', 'x_neg_correction', 'primal_per_spin'):
-            assert abs(getattr(cert, key) - ocert[key]) <= RTOL64 * max(1.0, abs(ocert[key])), key
+            assert abs(getattr(cert, key) - ocert[key]) <= rtol64(pb.D) * max(1.0, abs(ocert[key])), key
         assert abs(cert.x_min_eig - ocert['x_min_eig']) < 1e-9
     finally:
         ve.ve_destroy(h)
@@ -288,7 +296,9 @@ def test_mixed_precision_reaches_the_float64_bound(ve):
 def test_mixed_sweeps_track_the_oracle(ve, lattice, cluster):
     """Mixed-precision sweeps (float32 arithmetic in the pair pass, the DFT and both
     projections; float64 state and reductions) stay within float32 rounding of the float64
-    oracle: 2e-4 relative on the whole state after 30 sweeps."""
+    oracle: the whole state after 30 sweeps within 30 times the per-sweep bound of a float32
+    projection, 8 (D + 16) 2^-24, relative (the sweep is nonexpansive, so errors add at most
+    linearly): 4.6e-4 at D = 16, 3.9e-3 at D = 256."""
     pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 0.8, 1)))
     st = vo.initial_state(pb)
     h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 0.8),
@@ -298,7 +308,7 @@ def test_mixed_sweeps_track_the_oracle(ve, lattice, cluster):
         for _ in range(30):
             vo.iterate(pb, st)
         err = relerr(ve.ve_get_state(h), vo.pack_state(pb, st))
-        assert err < 2e-4, err
+        assert err < 30 * 8 * (pb.D + 16) * 2.0 ** -24, err
         cert = ve.ve_bound(h)
         assert abs(cert.bound_per_spin - vo.certified_bound(pb, st)['bound_per_spin']) < 1e-3
     finally:
