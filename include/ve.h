@@ -166,6 +166,26 @@ int ve_profile_sweeps(ve_handle* h, double* pair, double* wavevector);
 /* Name of a status code (static string). */
 const char* ve_error_string(int code);
 
+/* ---- batches of independent instances ----------------------------------------------------
+ * n independent instances (any mix of lattices, cluster sizes, Hamiltonians) advanced together:
+ * each sweep of the batch is one CUDA graph launch whose branches are the sweeps of the
+ * instances, so small instances that would leave most of the GPU idle run concurrently.  Every
+ * instance keeps its own state, convergence test and precision phase and stops when it
+ * converges; its iterates are identical to those of a single handle run with the same calls.
+ * opt applies to every instance (opt->stream must be NULL: each instance gets a stream).
+ * ve_batch_iterate writes n statuses to `out` (host, may be NULL) and returns VE_OK when every
+ * instance converged (or tol <= 0), else VE_NOT_CONVERGED / VE_ENONFINITE / VE_ECUDA.
+ * ve_batch_handle gives instance i for ve_get_state / ve_set_state / ve_bound (owned by the
+ * batch; do not destroy it, and do not call ve_iterate or ve_profile on it). */
+typedef struct ve_batch ve_batch;
+int ve_create_batch(int n, const ve_lattice* lattices, const ve_cluster* clusters,
+                    const ve_hamiltonian* hams, const ve_options* opt, ve_batch** out);
+int ve_batch_size(const ve_batch* b);
+ve_handle* ve_batch_handle(ve_batch* b, int i);
+int ve_batch_iterate(ve_batch* b, long max_iter, double tol, ve_status* out);
+int ve_batch_bound(ve_batch* b, ve_cert* out);
+void ve_batch_destroy(ve_batch* b);
+
 /* ---- batched building blocks on caller device memory ------------------------------------ */
 
 /* Pi_{>=0} (Sec. 3, the Frobenius-nearest PSD matrix, Eq. (rhoijTildeUpdate)) of `count` real

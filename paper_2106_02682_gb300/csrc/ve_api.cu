@@ -660,21 +660,51 @@ int ve_get_status(ve_handle* h, ve_status* out) {
   return read_status(h, out);
 }
 
+// Stopping rule shared by ve_iterate and ve_batch_iterate: in VE_PREC_MIXED, float32 sweeps
+// until the residual meets tol or has not fallen by 1 % over 100 read-backs (the float32
+// rounding floor), then float64 sweeps until the residual meets tol.
+struct IterCtl {
+  double best = INFINITY;
+  int stall = 0;
+  bool finished = false;
+  int rc = VE_NOT_CONVERGED;
+};
+
+void ctl_update(ve_handle* h, IterCtl& c, const ve_status& s, double tol) {
+  if (!isfinite(s.energy_per_spin) || !isfinite(s.feas_err)) {
+    c.finished = true;
+    c.rc = VE_ENONFINITE;
+    return;
+  }
+  if (tol <= 0) return;
+  const bool fp32 = h->opt.precision == VE_PREC_MIXED && !h->fp64_phase;
+  if (fp32) {
+    if (s.residual < 0.99 * c.best) {
+      c.best = s.residual;
+      c.stall = 0;
+    } else {
+      ++c.stall;
+    }
+    if (s.residual <= tol || c.stall >= 100) h->fp64_phase = true;
+  } else if (s.residual <= tol) {
+    c.finished = true;
+    c.rc = VE_OK;
+  }
+}
+
 int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out) {
   if (!h || max_iter < 0) return VE_EINVAL;
   DeviceGuard g(h->device);
   const bool mixed = h->opt.precision == VE_PREC_MIXED;
   ve_status s;
-  int rc = VE_NOT_CONVERGED;
+  IterCtl c;
   long done = 0;
-  double best = INFINITY;
-  int stall = 0;
   if (max_iter == 0) {
     int r = read_status(h, &s);
     if (out) *out = s;
     return r != VE_OK ? r : VE_OK;
   }
-  while (done < max_iter) {
+  while (done < max_iter && !c.finished) {
     const long chunk = (long)h->opt.check_every < max_iter - done ? (long)h->opt.check_every : max_iter - done;
     const bool fp32 = mixed && !h->fp64_phase;
     int r = run_sweeps(h, chunk, fp32);
@@ -682,30 +712,12 @@ int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out) {
     r = read_status(h, &s);
     if (r != VE_OK) return r;
     done += chunk;
-    if (!isfinite(s.energy_per_spin) || !isfinite(s.feas_err)) {
-      if (out) *out = s;
-      return VE_ENONFINITE;
-    }
-    if (tol > 0) {
-      if (fp32) {
-        // float32 projections until the residual meets the target or has not fallen by 1 %
-        // over 100 read-backs (the float32 rounding floor); float64 sweeps then finish the solve
-        if (s.residual < 0.99 * best) {
-          best = s.residual;
-          stall = 0;
-        } else {
-          ++stall;
-        }
-        if (s.residual <= tol || stall >= 100) h->fp64_phase = true;
-      } else if (s.residual <= tol) {
-        rc = VE_OK;
-        break;
-      }
-    }
+    ctl_update(h, c, s, tol);
   }
-  if (tol <= 0) rc = VE_OK;
   if (out) *out = s;
-  return rc;
+  if (c.rc == VE_ENONFINITE) return VE_ENONFINITE;
+  if (tol <= 0) return VE_OK;
+  return c.rc;
 }
 
 int ve_bound(ve_handle* h, ve_cert* out) {
@@ -806,6 +818,206 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
   VE_CU(launch_xproj(p, spec, canon, fp32, nullptr, 0, s));
   VE_CU(fft_inverse(p, spec, A, B, x_out, tw, fp32, s));
   return VE_OK;
+}
+
+
+// ------------------------------------------------------------------------- batches
+}  // extern "C"
+
+struct ve_batch {
+  int n = 0;
+  int device = 0;
+  std::vector<ve_handle*> h;
+  cudaStream_t main = nullptr;
+  DevStatus* dst = nullptr;  // device, n entries (the instances' status words)
+  DevStatus* hst = nullptr;  // pinned mirror
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> key;  // per instance: -1 idle, 0 float64 branch, 1 float32 branch
+};
+
+namespace {
+
+void batch_drop_graph(ve_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->key.clear();
+}
+
+// One graph whose branches are one sweep of every instance with key >= 0 (fork on the main
+// stream, one branch per instance stream, join back).
+int batch_capture(ve_batch* b, const std::vector<int>& key) {
+  batch_drop_graph(b);
+  VE_CU(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(b->fork, b->main);
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+    if (key[i] < 0) continue;
+    ve_handle* h = b->h[i];
+    e = cudaStreamWaitEvent(h->stream, b->fork, 0);
+    if (e == cudaSuccess) e = issue_sweep(h, key[i] == 1, true);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join[i], h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->main, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return VE_ECUDA;
+  }
+  b->graph = g;
+  VE_CU(cudaGraphInstantiate(&b->exec, g, 0));
+  b->key = key;
+  return VE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ve_create_batch(int n, const ve_lattice* lattices, const ve_cluster* clusters,
+                    const ve_hamiltonian* hams, const ve_options* opt, ve_batch** out) {
+  if (!out || n < 1 || !lattices || !clusters || !hams) return VE_EINVAL;
+  *out = nullptr;
+  if (opt && opt->stream) return VE_EINVAL;  // every instance runs on a stream of its own
+  ve_batch* b = new (std::nothrow) ve_batch();
+  if (!b) return VE_ENOMEM;
+  cudaGetDevice(&b->device);
+  b->n = n;
+  b->h.assign(n, nullptr);
+  b->join.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    const int rc = ve_create(&lattices[i], &clusters[i], &hams[i], opt, &b->h[i]);
+    if (rc != VE_OK) {
+      ve_batch_destroy(b);
+      return rc;
+    }
+  }
+  if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc((void**)&b->dst, sizeof(DevStatus) * n) != cudaSuccess ||
+      cudaMallocHost((void**)&b->hst, sizeof(DevStatus) * n) != cudaSuccess) {
+    cudaGetLastError();
+    ve_batch_destroy(b);
+    return VE_ENOMEM;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) {
+      ve_batch_destroy(b);
+      return VE_ECUDA;
+    }
+    // the instance's status word moves into the batch array, so one copy reads them all
+    ve_handle* h = b->h[i];
+    b->hst[i] = *h->hst;
+    h->dst = b->dst + i;
+  }
+  if (cudaMemcpy(b->dst, b->hst, sizeof(DevStatus) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    ve_batch_destroy(b);
+    return VE_ECUDA;
+  }
+  *out = b;
+  return VE_OK;
+}
+
+int ve_batch_size(const ve_batch* b) { return b ? b->n : 0; }
+
+ve_handle* ve_batch_handle(ve_batch* b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->h[i];
+}
+
+int ve_batch_iterate(ve_batch* b, long max_iter, double tol, ve_status* out) {
+  if (!b || max_iter < 0) return VE_EINVAL;
+  DeviceGuard g(b->device);
+  const int n = b->n;
+  std::vector<IterCtl> ctl(n);
+  std::vector<ve_status> st(n);
+  long done = 0;
+  int check = b->h[0]->opt.check_every;
+  for (int i = 1; i < n; ++i) check = b->h[i]->opt.check_every < check ? b->h[i]->opt.check_every : check;
+  while (done < max_iter) {
+    const long chunk = (long)check < max_iter - done ? (long)check : max_iter - done;
+    std::vector<int> key(n, -1);
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      if (ctl[i].finished) continue;
+      ve_handle* h = b->h[i];
+      const bool fp32 = h->opt.precision == VE_PREC_MIXED && !h->fp64_phase;
+      const int v = fp32 ? 1 : 0;
+      if (h->prof) return VE_EINVAL;  // per-stage profiling is per handle, not in a batch
+      if (!h->vvalid[v]) {
+        // first sweep in this precision: direct and cold, then the main stream waits for it
+        VE_CU(issue_sweep(h, fp32, false));
+        h->vvalid[v] = true;
+        VE_CU(cudaEventRecord(b->join[i], h->stream));
+        VE_CU(cudaStreamWaitEvent(b->main, b->join[i], 0));
+      }
+      key[i] = v;
+      any = true;
+    }
+    if (!any) break;
+    if (!b->exec || key != b->key) {
+      const int r = batch_capture(b, key);
+      if (r != VE_OK) return r;
+    }
+    for (long c = 0; c < chunk; ++c) VE_CU(cudaGraphLaunch(b->exec, b->main));
+    VE_CU(cudaMemcpyAsync(b->hst, b->dst, sizeof(DevStatus) * n, cudaMemcpyDeviceToHost, b->main));
+    VE_CU(cudaStreamSynchronize(b->main));
+    done += chunk;
+    for (int i = 0; i < n; ++i) {
+      if (ctl[i].finished) continue;
+      ve_handle* h = b->h[i];
+      *h->hst = b->hst[i];
+      st[i].iter = (long)b->hst[i].iter;
+      st[i].energy_per_spin = b->hst[i].energy;
+      st[i].feas_err = b->hst[i].feas;
+      st[i].d_energy = b->hst[i].d_energy;
+      st[i].residual = b->hst[i].residual;
+      ctl_update(h, ctl[i], st[i], tol);
+    }
+  }
+  int rc = VE_OK;
+  for (int i = 0; i < n; ++i) {
+    if (out) {
+      const int r = read_status(b->h[i], &out[i]);
+      if (r != VE_OK) return r;
+    }
+    if (ctl[i].rc == VE_ENONFINITE) rc = VE_ENONFINITE;
+    else if (tol > 0 && ctl[i].rc != VE_OK && rc == VE_OK) rc = VE_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+int ve_batch_bound(ve_batch* b, ve_cert* out) {
+  if (!b || !out) return VE_EINVAL;
+  for (int i = 0; i < b->n; ++i) {
+    const int r = ve_bound(b->h[i], &out[i]);
+    if (r != VE_OK) return r;
+  }
+  return VE_OK;
+}
+
+void ve_batch_destroy(ve_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  if (b->main) cudaStreamSynchronize(b->main);
+  batch_drop_graph(b);
+  for (int i = 0; i < (int)b->h.size(); ++i) {
+    if (b->h[i]) {
+      // give the instance back a status word of its own before it is released
+      b->h[i]->dst = nullptr;
+      ve_destroy(b->h[i]);
+    }
+    if (i < (int)b->join.size() && b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->main) cudaStreamDestroy(b->main);
+  if (b->dst) cudaFree(b->dst);
+  if (b->hst) cudaFreeHost(b->hst);
+  delete b;
 }
 
 }  // extern "C"

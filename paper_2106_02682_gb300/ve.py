@@ -99,6 +99,14 @@ def _load():
         "ve_profile": (c_int, [H, c_int]),
         "ve_profile_read": (c_int, [H, P_double, ctypes.POINTER(c_long)]),
         "ve_profile_sweeps": (c_int, [H, P_double, P_double]),
+        "ve_create_batch": (c_int, [c_int, ctypes.POINTER(ve_lattice), ctypes.POINTER(ve_cluster),
+                                    ctypes.POINTER(ve_hamiltonian), ctypes.POINTER(ve_options),
+                                    ctypes.POINTER(c_void_p)]),
+        "ve_batch_size": (c_int, [c_void_p]),
+        "ve_batch_handle": (c_void_p, [c_void_p, c_int]),
+        "ve_batch_iterate": (c_int, [c_void_p, c_long, c_double, ctypes.POINTER(ve_status)]),
+        "ve_batch_bound": (c_int, [c_void_p, ctypes.POINTER(ve_cert)]),
+        "ve_batch_destroy": (None, [c_void_p]),
         "ve_project_psd_sym": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
         "ve_project_psd_herm": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
         "ve_circulant_workspace_size": (c_size_t, [c_int, ctypes.POINTER(c_int), c_int]),
@@ -280,3 +288,42 @@ def ve_circulant_project_noalloc(x_in_ptr, x_out_ptr, M, D, precision=VE_PREC_FP
     return _check(_lib.ve_circulant_project_noalloc(x_in_ptr, x_out_ptr, dim, arr, int(D),
                                                     int(precision), stream),
                   "ve_circulant_project_noalloc")
+
+
+def ve_create_batch(instances, opt=None):
+    """instances: list of (lattice extents, cluster extents, ve_hamiltonian).  Returns a batch."""
+    n = len(instances)
+    lats = (ve_lattice * n)(*[make_lattice(l) for l, _, _ in instances])
+    clus = (ve_cluster * n)(*[make_cluster(c) for _, c, _ in instances])
+    hams = (ve_hamiltonian * n)(*[hm for _, _, hm in instances])
+    b = c_void_p()
+    _check(_lib.ve_create_batch(n, lats, clus, hams, ctypes.byref(opt) if opt is not None else None,
+                                ctypes.byref(b)), "ve_create_batch")
+    return b.value
+
+
+def ve_batch_size(b):
+    return _lib.ve_batch_size(c_void_p(b))
+
+
+def ve_batch_handle(b, i):
+    return _lib.ve_batch_handle(c_void_p(b), int(i))
+
+
+def ve_batch_iterate(b, max_iter, tol=0.0):
+    n = ve_batch_size(b)
+    st = (ve_status * n)()
+    code = _check(_lib.ve_batch_iterate(c_void_p(b), int(max_iter), float(tol), st),
+                  "ve_batch_iterate")
+    return code, list(st)
+
+
+def ve_batch_bound(b):
+    n = ve_batch_size(b)
+    c = (ve_cert * n)()
+    _check(_lib.ve_batch_bound(c_void_p(b), c), "ve_batch_bound")
+    return list(c)
+
+
+def ve_batch_destroy(b):
+    _lib.ve_batch_destroy(c_void_p(b) if b else None)

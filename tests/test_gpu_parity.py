@@ -313,3 +313,34 @@ def test_mixed_sweeps_track_the_oracle(ve, lattice, cluster):
         assert abs(cert.bound_per_spin - vo.certified_bound(pb, st)['bound_per_spin']) < 1e-3
     finally:
         ve.ve_destroy(h)
+
+
+# ------------------------------------------------------------------ batches of instances
+
+BATCH = [((100,), (2,), "tfim", 1.0), ((16,), (1,), "tfim", 0.5), ((24,), (2,), "xxz", 0.8),
+         ((4, 4), (1, 1), "tfim", 2.0), ((12,), (3,), "xxz", 1.0), ((96,), (2,), "tfim", 1.5)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_reproduces_single_handles(ve, prec):
+    """A batch advances every instance exactly as a single handle would: same states bit for
+    bit after a fixed number of sweeps and, with a tolerance, the same stopping sweep."""
+    opt = ve.ve_default_options(precision=prec)
+    inst = [(lat, clu, _ham(ve, kind, len(lat), x)) for lat, clu, kind, x in BATCH]
+    for max_iter, tol in ((40, 0.0), (3000, 1e-4)):
+        b = ve.ve_create_batch(inst, opt)
+        try:
+            code, sts = ve.ve_batch_iterate(b, max_iter, tol)
+            states = [ve.ve_get_state(ve.ve_batch_handle(b, i)) for i in range(len(inst))]
+            certs = ve.ve_batch_bound(b)
+        finally:
+            ve.ve_batch_destroy(b)
+        for i, (lat, clu, hm) in enumerate(inst):
+            h = ve.ve_create(lat, clu, hm, opt)
+            try:
+                c1, s1 = ve.ve_iterate(h, max_iter, tol)
+                np.testing.assert_array_equal(states[i], ve.ve_get_state(h))
+                assert s1.iter == sts[i].iter and s1.residual == sts[i].residual
+                assert ve.ve_bound(h).bound_per_spin == certs[i].bound_per_spin
+            finally:
+                ve.ve_destroy(h)
