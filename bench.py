@@ -21,6 +21,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -224,7 +226,6 @@ def workload_config(args, N, D):
 
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
-    import numpy as np
     import torch
     world, rank, local = dist_env()
     if world > 1:
@@ -327,6 +328,11 @@ def run_ours(args):
                   for s in prof}
         launches = int(sum(v[1] for v in prof.values()))
 
+        # ---- a batch of 64 paper-size instances against one-at-a-time handles
+        batch = None
+        if not args.no_ttb and rank == 0:
+            batch = batch_rate(ve, synth, "paper", 64, 200, ve.VE_PREC_FP64)
+
         # ---- time to certified bound, float64 and mixed, fresh handles
         ttb = None
         if not args.no_ttb and rank == 0:
@@ -358,7 +364,7 @@ def run_ours(args):
             "data": "synthetic (seeded spin Hamiltonian, no dataset)",
             "config": workload_config(args, N, D),
             "e2e": e2e, "gpu_launches": launches * world, "roofline": roof, "stages": stages,
-            "clocks": ck, "time_to_bound": ttb,
+            "clocks": ck, "time_to_bound": ttb, "batch": batch,
             "jacobi_sweeps_per_eigensolve": {"pair": jac_pair, "wavevector": jac_k},
             "last_status": {"iter": status.iter, "energy_per_spin": status.energy_per_spin,
                             "feas_err": status.feas_err},
@@ -376,10 +382,67 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batches
+def batch_rate(ve, synth, family, count, sweeps, prec, stream=None):
+    """Instance-sweeps per second of a batch (one graph launch per sweep) and of the same
+    instances advanced one handle at a time."""
+    import torch
+    inst = synth.batch_instances(family, count)
+    triples = [(d["lattice"], d["cluster"],
+                ve.ve_ham_tfim(1, 1.0, d["x"]) if d["kind"] == "tfim" else ve.ve_ham_xxz(1, 1.0, d["x"]))
+               for d in inst]
+    opt = ve.ve_default_options(precision=prec)
+    b = ve.ve_create_batch(triples, opt)
+    try:
+        ve.ve_batch_iterate(b, 3, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ve.ve_batch_iterate(b, sweeps, 0.0)
+        el_b = time.perf_counter() - t0
+    finally:
+        ve.ve_batch_destroy(b)
+    el_s = 0.0
+    for tr in triples:
+        h = ve.ve_create(*tr, opt)
+        try:
+            ve.ve_iterate(h, 3, 0.0)
+            t0 = time.perf_counter()
+            ve.ve_iterate(h, sweeps, 0.0)
+            el_s += time.perf_counter() - t0
+        finally:
+            ve.ve_destroy(h)
+    clusters = sum(int(np.prod(d["lattice"])) // int(np.prod(d["cluster"])) for d in inst)
+    return {"family": family, "instances": count, "clusters_total": clusters,
+            "precision": "mixed" if prec else "fp64", "sweeps": sweeps,
+            "batched_instance_sweeps_per_s": count * sweeps / el_b,
+            "one_at_a_time_instance_sweeps_per_s": count * sweeps / el_s,
+            "speedup": el_s / el_b}
+
+
+def run_batch(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02682_gb300 import synth, ve
+    prec = ve.VE_PREC_FP64 if args.precision == "fp64" else ve.VE_PREC_MIXED
+    fam = args.workload.split("_", 1)[1]
+    count = 256 if fam == "c4" else 64
+    r = batch_rate(ve, synth, fam, count, args.steps, prec)
+    print(json.dumps({"metric": METRIC, "value": r["batched_instance_sweeps_per_s"],
+                      "unit": "instance-sweeps/s", "n_gpus": 1, "steps": args.steps,
+                      "warmup": 3, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32+f64",
+                      "data": "synthetic", "config": {"workload": args.workload, **r},
+                      "timing": "wall clock around ve_batch_iterate / ve_iterate, no L2 flush"}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("batch_"):
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -6,7 +6,8 @@ Only random-matrix and workload generators live here (no step of the solver's ar
     share with repeated eigenvalues and low rank, which stress the eigensolvers;
   * circulant_first_row: a first block row X_{0,delta} obeying X_{0,-delta} = X_{0,delta}^T, the
     structure of the dual matrix in Algorithm 6;
-  * workloads: the named benchmark instances (lattice, cluster, field) used by bench.py.
+  * workloads: the named benchmark instances (lattice, cluster, field) used by bench.py;
+  * batch_instances: seeded families of independent instances for batched runs.
 The default seed is 20210604.
 """
 import numpy as np
@@ -82,3 +83,40 @@ WORKLOADS = {
     # 2-D square lattice 64 x 64, h = 3, 2 x 2 clusters (256 x 256 pair marginals), 32 x 32 clusters
     "tfim2d_L4_32x32": dict(lattice=(64, 64), cluster=(2, 2), h=3.0, kind="tfim"),
 }
+
+
+def _supported_clusters(n):
+    """Nearest cluster count to n that the solver's block DFT supports for a 1-D chain: any n
+    up to 64, else n = n1 * n2 with n1, n2 <= 64."""
+    def ok(k):
+        if 2 <= k <= 64:
+            return True
+        return 64 < k <= 4096 and any(k % a == 0 and k // a <= 64 for a in range(2, 65))
+    for d in range(0, 4096):
+        for k in (n - d, n + d):
+            if ok(k):
+                return k
+    raise ValueError(n)
+
+
+def batch_instances(family="c4", count=256, seed=None):
+    """Independent 1-D instances: list of dict(kind, x, lattice, cluster).
+
+    c4:    half TFI (h ~ U[0.2, 2.0]), half XXZ (Delta ~ U[0, 1.5]); chain length log-uniform in
+           [64, 8192] spins; 2- or 3-spin clusters (16 x 16 or 64 x 64 pair marginals); the
+           cluster count is rounded to one the block DFT supports.
+    paper: TFI chains of 100 spins with 2-spin clusters (the paper's table instance), h ~ U[0.2, 2].
+    """
+    rng = _rng(seed)
+    out = []
+    for i in range(count):
+        if family == "paper":
+            out.append(dict(kind="tfim", x=float(rng.uniform(0.2, 2.0)), lattice=(100,), cluster=(2,)))
+            continue
+        kind = "tfim" if i < count // 2 else "xxz"
+        x = float(rng.uniform(0.2, 2.0) if kind == "tfim" else rng.uniform(0.0, 1.5))
+        L = int(rng.integers(2, 4))
+        length = float(np.exp(rng.uniform(np.log(64), np.log(8192))))
+        n = _supported_clusters(max(2, int(round(length / L))))
+        out.append(dict(kind=kind, x=x, lattice=(n * L,), cluster=(L,)))
+    return out
