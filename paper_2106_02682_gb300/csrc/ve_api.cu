@@ -941,29 +941,38 @@ int ve_batch_iterate(ve_batch* b, long max_iter, double tol, ve_status* out) {
   while (done < max_iter) {
     const long chunk = (long)check < max_iter - done ? (long)check : max_iter - done;
     std::vector<int> key(n, -1);
-    bool any = false;
+    bool any = false, cold = false;
     for (int i = 0; i < n; ++i) {
       if (ctl[i].finished) continue;
       ve_handle* h = b->h[i];
-      const bool fp32 = h->opt.precision == VE_PREC_MIXED && !h->fp64_phase;
-      const int v = fp32 ? 1 : 0;
       if (h->prof) return VE_EINVAL;  // per-stage profiling is per handle, not in a batch
-      if (!h->vvalid[v]) {
-        // first sweep in this precision: direct and cold, then the main stream waits for it
-        VE_CU(issue_sweep(h, fp32, false));
+      const bool fp32 = h->opt.precision == VE_PREC_MIXED && !h->fp64_phase;
+      key[i] = fp32 ? 1 : 0;
+      any = true;
+      if (!h->vvalid[key[i]]) cold = true;
+    }
+    if (!any) break;
+    long launches = chunk;
+    if (cold) {
+      // some instance starts a precision phase: its first sweep runs directly and cold (as in
+      // run_sweeps), and every other active instance takes one direct warm sweep beside it so
+      // that all advance by exactly `chunk` sweeps; the main stream then waits for them all
+      for (int i = 0; i < n; ++i) {
+        if (key[i] < 0) continue;
+        ve_handle* h = b->h[i];
+        const int v = key[i];
+        VE_CU(issue_sweep(h, v == 1, h->vvalid[v]));
         h->vvalid[v] = true;
         VE_CU(cudaEventRecord(b->join[i], h->stream));
         VE_CU(cudaStreamWaitEvent(b->main, b->join[i], 0));
       }
-      key[i] = v;
-      any = true;
+      --launches;
     }
-    if (!any) break;
-    if (!b->exec || key != b->key) {
+    if (launches > 0 && (!b->exec || key != b->key)) {
       const int r = batch_capture(b, key);
       if (r != VE_OK) return r;
     }
-    for (long c = 0; c < chunk; ++c) VE_CU(cudaGraphLaunch(b->exec, b->main));
+    for (long c = 0; c < launches; ++c) VE_CU(cudaGraphLaunch(b->exec, b->main));
     VE_CU(cudaMemcpyAsync(b->hst, b->dst, sizeof(DevStatus) * n, cudaMemcpyDeviceToHost, b->main));
     VE_CU(cudaStreamSynchronize(b->main));
     done += chunk;
