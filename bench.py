@@ -356,6 +356,40 @@ def run_ours(args):
                                   "iter_per_s": st.iter / el}
                 finally:
                     ve.ve_destroy(hh)
+            # learned warm start: trained on 24 instances of the same family whose fields avoid
+            # the evaluated one, then a mixed-precision solve from its prediction
+            from paper_2106_02682_gb300.warmstart import WarmStart
+            wsf = WarmStart(tw_["lattice"], tw_["cluster"], tw_["kind"], n_components=16)
+            try:
+                xs = np.linspace(0.2, 2.0, 24) + 0.0371
+                t0 = time.perf_counter()
+                states, _ = wsf.training_states(xs, tol=1e-7, max_iter=60000)
+                t_solves = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                fit_loss = wsf.fit(xs, states, train_steps=4000)
+                t_fit = time.perf_counter() - t0
+                hh = ve.ve_create(tw_["lattice"], tw_["cluster"], tham,
+                                  ve.ve_default_options(precision=ve.VE_PREC_MIXED,
+                                                        stream=stream.cuda_stream))
+                try:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    wsf.apply(hh, tw_["h"])
+                    code, st = ve.ve_iterate(hh, args.ttb_max_iter, 1e-6)
+                    cert = ve.ve_bound(hh)
+                    el = time.perf_counter() - t0
+                    ttb["warm_mixed"] = {"seconds": el, "sweeps": st.iter, "converged": code == 0,
+                                         "residual": st.residual,
+                                         "bound_per_spin": cert.bound_per_spin,
+                                         "primal_per_spin": cert.primal_per_spin,
+                                         "training": {"instances": len(xs),
+                                                      "solve_seconds": t_solves,
+                                                      "fit_seconds": t_fit, "fit_loss": fit_loss,
+                                                      "pca_explained": wsf.explained}}
+                finally:
+                    ve.ve_destroy(hh)
+            finally:
+                wsf.close()
 
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -186,6 +186,35 @@ int ve_batch_iterate(ve_batch* b, long max_iter, double tol, ve_status* out);
 int ve_batch_bound(ve_batch* b, ve_cert* out);
 void ve_batch_destroy(ve_batch* b);
 
+/* Project the handle's X onto the PSD cone in place (block DFT, per-wavevector projection in
+ * float64, inverse DFT -- the last three steps of Algorithm 6 without the G term).  Used after
+ * ve_set_state with a predicted state: the certified bound needs X >= 0 and then holds whatever
+ * the prediction was.  Synchronous.  Errors: VE_EINVAL, VE_ECUDA. */
+int ve_project_state_x(ve_handle* h);
+
+/* ---- learned warm start ------------------------------------------------------------------
+ * The paper has no learned component.  This is a float32 multilayer perceptron
+ *   a_0 = x, a_l = tanh(W_l a_{l-1} + b_l) (n_layers hidden layers of width n_hidden),
+ *   y = W_out a_{n_layers} + b_out,
+ * trained on the GPU by full-batch Adam (beta 0.9 / 0.999) on loss = mean over samples and
+ * outputs of (y - t)^2 / 2, with hand-written forward, backward and update kernels.  It maps
+ * model parameters to a compressed warm-start state (see paper_2106_02682_gb300/warmstart.py).
+ * Parameters are stored layer by layer: W (outputs x inputs, row-major) then b; initial weights
+ * are Glorot-uniform from `seed`, biases zero.  x (n x n_in), t (n x n_out), y (n x n_out) and
+ * grad (num_params) are host arrays, row-major.  All calls are synchronous.
+ * Errors: VE_EINVAL (sizes, NULL), VE_ENOMEM, VE_ECUDA. */
+typedef struct ve_mlp ve_mlp;
+int ve_mlp_create(int n_in, int n_hidden, int n_layers, int n_out, unsigned long long seed,
+                  ve_mlp** out);
+void ve_mlp_destroy(ve_mlp* m);
+size_t ve_mlp_num_params(const ve_mlp* m);
+int ve_mlp_get_params(ve_mlp* m, float* host, size_t count);
+int ve_mlp_set_params(ve_mlp* m, const float* host, size_t count);  /* also resets Adam */
+int ve_mlp_loss_grad(ve_mlp* m, const float* x, const float* t, int n, float* loss, float* grad);
+int ve_mlp_train(ve_mlp* m, const float* x, const float* t, int n, int steps, float lr,
+                 float* loss_out);
+int ve_mlp_predict(ve_mlp* m, const float* x, int n, float* y);
+
 /* ---- batched building blocks on caller device memory ------------------------------------ */
 
 /* Pi_{>=0} (Sec. 3, the Frobenius-nearest PSD matrix, Eq. (rhoijTildeUpdate)) of `count` real

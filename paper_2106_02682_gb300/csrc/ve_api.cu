@@ -766,6 +766,17 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   return VE_OK;
 }
 
+int ve_project_state_x(ve_handle* h) {
+  if (!h) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  double2* spec = nullptr;
+  VE_CU(fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, false, h->stream));
+  VE_CU(launch_xproj(h->plan, spec, h->canon, false, nullptr, 0, h->stream, nullptr, h->gws));
+  VE_CU(fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, false, h->stream));
+  VE_CU(cudaStreamSynchronize(h->stream));
+  return VE_OK;
+}
+
 int ve_project_psd_sym(const double* in, double* out, int n, long count, int precision,
                        void* stream) {
   if (!in || !out || count < 0) return VE_EINVAL;

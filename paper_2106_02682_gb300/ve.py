@@ -31,6 +31,7 @@ STAGES = ("pair", "rho0", "dual12", "status", "fft_forward", "xproj", "fft_inver
 c_int, c_long, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_long, ctypes.c_double,
                                                ctypes.c_void_p, ctypes.c_size_t)
 P_double = ctypes.POINTER(c_double)
+P_float = ctypes.POINTER(ctypes.c_float)
 
 
 class ve_lattice(ctypes.Structure):
@@ -107,6 +108,16 @@ def _load():
         "ve_batch_iterate": (c_int, [c_void_p, c_long, c_double, ctypes.POINTER(ve_status)]),
         "ve_batch_bound": (c_int, [c_void_p, ctypes.POINTER(ve_cert)]),
         "ve_batch_destroy": (None, [c_void_p]),
+        "ve_project_state_x": (c_int, [H]),
+        "ve_mlp_create": (c_int, [c_int, c_int, c_int, c_int, ctypes.c_ulonglong,
+                                  ctypes.POINTER(c_void_p)]),
+        "ve_mlp_destroy": (None, [c_void_p]),
+        "ve_mlp_num_params": (c_size_t, [c_void_p]),
+        "ve_mlp_get_params": (c_int, [c_void_p, P_float, c_size_t]),
+        "ve_mlp_set_params": (c_int, [c_void_p, P_float, c_size_t]),
+        "ve_mlp_loss_grad": (c_int, [c_void_p, P_float, P_float, c_int, P_float, P_float]),
+        "ve_mlp_train": (c_int, [c_void_p, P_float, P_float, c_int, c_int, ctypes.c_float, P_float]),
+        "ve_mlp_predict": (c_int, [c_void_p, P_float, c_int, P_float]),
         "ve_project_psd_sym": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
         "ve_project_psd_herm": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
         "ve_circulant_workspace_size": (c_size_t, [c_int, ctypes.POINTER(c_int), c_int]),
@@ -327,3 +338,65 @@ def ve_batch_bound(b):
 
 def ve_batch_destroy(b):
     _lib.ve_batch_destroy(c_void_p(b) if b else None)
+
+
+def ve_project_state_x(h):
+    _check(_lib.ve_project_state_x(c_void_p(h)), "ve_project_state_x")
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(P_float)
+
+
+def ve_mlp_create(n_in, n_hidden, n_layers, n_out, seed=20210604):
+    m = c_void_p()
+    _check(_lib.ve_mlp_create(int(n_in), int(n_hidden), int(n_layers), int(n_out), int(seed),
+                              ctypes.byref(m)), "ve_mlp_create")
+    return m.value
+
+
+def ve_mlp_destroy(m):
+    _lib.ve_mlp_destroy(c_void_p(m) if m else None)
+
+
+def ve_mlp_num_params(m):
+    return _lib.ve_mlp_num_params(c_void_p(m))
+
+
+def ve_mlp_get_params(m):
+    out = np.empty(ve_mlp_num_params(m), dtype=np.float32)
+    _check(_lib.ve_mlp_get_params(c_void_p(m), out.ctypes.data_as(P_float), out.size), "ve_mlp_get_params")
+    return out
+
+
+def ve_mlp_set_params(m, params):
+    p, pp = _f32(params)
+    _check(_lib.ve_mlp_set_params(c_void_p(m), pp, p.size), "ve_mlp_set_params")
+
+
+def ve_mlp_loss_grad(m, x, t):
+    x, xp = _f32(x)
+    t, tp = _f32(t)
+    loss = ctypes.c_float()
+    g = np.empty(ve_mlp_num_params(m), dtype=np.float32)
+    _check(_lib.ve_mlp_loss_grad(c_void_p(m), xp, tp, x.shape[0], ctypes.byref(loss),
+                                 g.ctypes.data_as(P_float)), "ve_mlp_loss_grad")
+    return loss.value, g
+
+
+def ve_mlp_train(m, x, t, steps, lr=1e-3):
+    x, xp = _f32(x)
+    t, tp = _f32(t)
+    loss = ctypes.c_float()
+    _check(_lib.ve_mlp_train(c_void_p(m), xp, tp, x.shape[0], int(steps), float(lr),
+                             ctypes.byref(loss)), "ve_mlp_train")
+    return loss.value
+
+
+def ve_mlp_predict(m, x, n_out):
+    x, xp = _f32(x)
+    y = np.empty((x.shape[0], n_out), dtype=np.float32)
+    _check(_lib.ve_mlp_predict(c_void_p(m), xp, x.shape[0], y.ctypes.data_as(P_float)),
+           "ve_mlp_predict")
+    return y

@@ -1,0 +1,72 @@
+"""The learned warm start: the GPU network against the CPU float64 reference, and the warm start
+against cold starts on held-out parameters."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle import mlp
+from oracle import models as mo
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ve():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    __graft_entry__.build()
+    from paper_2106_02682_gb300 import ve as mod
+    return mod
+
+
+@pytest.mark.parametrize("n_in,hidden,layers,n_out,n", [(1, 256, 3, 16, 37), (3, 40, 2, 5, 9)])
+def test_gpu_network_matches_the_reference(ve, n_in, hidden, layers, n_out, n):
+    rng = np.random.default_rng(7)
+    m = ve.ve_mlp_create(n_in, hidden, layers, n_out, 11)
+    try:
+        shapes = mlp.layer_shapes(n_in, hidden, layers, n_out)
+        assert ve.ve_mlp_num_params(m) == sum(o * i + o for o, i in shapes)
+        p = ve.ve_mlp_get_params(m).astype(np.float64)
+        x = rng.normal(size=(n, n_in)).astype(np.float32)
+        t = rng.normal(size=(n, n_out)).astype(np.float32)
+        loss, g = ve.ve_mlp_loss_grad(m, x, t)
+        rloss, rg = mlp.loss_grad(p, shapes, x, t)
+        assert abs(loss - rloss) <= 1e-5 * max(1.0, abs(rloss))
+        assert np.max(np.abs(g - rg)) <= 1e-4 * np.max(np.abs(rg))
+        y = ve.ve_mlp_predict(m, x, n_out)
+        np.testing.assert_allclose(y, mlp.forward(p, shapes, x)[-1], atol=2e-5, rtol=1e-4)
+        # training lowers the loss
+        assert ve.ve_mlp_train(m, x, t, 300, 1e-3) < 0.5 * rloss
+    finally:
+        ve.ve_mlp_destroy(m)
+
+
+def test_warm_start_beats_cold_start_on_held_out_fields(ve):
+    from paper_2106_02682_gb300.warmstart import WarmStart
+    lattice, cluster = (40,), (2,)
+    ws = WarmStart(lattice, cluster, "tfim", n_components=12)
+    try:
+        xs = np.linspace(0.5, 1.5, 11)
+        states, _ = ws.training_states(xs, tol=1e-8, max_iter=40000)
+        assert ws.fit(xs, states, train_steps=3000) < 1e-2
+        opt = ve.ve_default_options(precision=1)
+        cold_total = warm_total = 0
+        for h in (0.65, 0.95, 1.25):
+            hc = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, h), opt)
+            hw = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, h), opt)
+            try:
+                _, sc = ve.ve_iterate(hc, 40000, 1e-6)
+                ws.apply(hw, h)
+                assert ve.ve_bound(hw).x_min_eig > -1e-9          # X is PSD after the projection
+                _, sw = ve.ve_iterate(hw, 40000, 1e-6)
+                cold_total += sc.iter
+                warm_total += sw.iter
+                bound = ve.ve_bound(hw).bound_per_spin
+                assert bound <= mo.tfim_chain_jw_energy(40, 1.0, h) / 40     # still a lower bound
+            finally:
+                ve.ve_destroy(hc)
+                ve.ve_destroy(hw)
+        assert warm_total < 0.7 * cold_total, (warm_total, cold_total)
+    finally:
+        ws.close()

@@ -400,3 +400,25 @@ def test_bound_below_jordan_wigner_energy_long_chain():
     st = vo.initial_state(pb)
     vo.run(pb, st, 300)
     assert vo.certified_bound(pb, st)['bound_per_spin'] <= mo.tfim_chain_jw_energy(64, 1.0, 1.0) / 64
+
+
+# ------------------------------------------------------------------ warm-start network (CPU reference)
+
+def test_mlp_reference_gradient_matches_finite_differences():
+    from oracle import mlp
+    shapes = mlp.layer_shapes(2, 7, 2, 3)
+    n = sum(o * i + o for o, i in shapes)
+    params = rng.normal(scale=0.5, size=n)
+    x = rng.normal(size=(5, 2))
+    t = rng.normal(size=(5, 3))
+    loss, g = mlp.loss_grad(params, shapes, x, t)
+    fd = np.empty(n)
+    h = 1e-6
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fd[i] = (mlp.loss_grad(params + e, shapes, x, t)[0] - mlp.loss_grad(params - e, shapes, x, t)[0]) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+    # the loss is the stated mean of squared residuals / 2
+    y = mlp.forward(params, shapes, x)[-1]
+    assert abs(loss - 0.5 * np.mean((y - t) ** 2)) < 1e-15
