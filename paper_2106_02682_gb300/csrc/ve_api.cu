@@ -327,9 +327,13 @@ int read_status(ve_handle* h, ve_status* out) {
   return VE_OK;
 }
 
+// Entry points that launch work start from a clean error state: a failed runtime call made
+// earlier by the caller (not a device fault, which stays sticky) must not be reported as this
+// call's launch failure.
 class DeviceGuard {
  public:
   explicit DeviceGuard(int dev) {
+    cudaGetLastError();
     cudaGetDevice(&old_);
     if (old_ != dev) cudaSetDevice(dev);
     dev_ = dev;
@@ -410,6 +414,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   *out = nullptr;
   ve_handle* h = new (std::nothrow) ve_handle();
   if (!h) return VE_ENOMEM;
+  cudaGetLastError();  // report only errors raised by this call
   int rc = build_model(lattice, cluster, ham, h->md);
   if (rc != VE_OK) {
     delete h;
@@ -779,6 +784,7 @@ int ve_project_state_x(ve_handle* h) {
 
 int ve_project_psd_sym(const double* in, double* out, int n, long count, int precision,
                        void* stream) {
+  cudaGetLastError();  // report only errors raised by this call
   if (!in || !out || count < 0) return VE_EINVAL;
   if (n != 2 && n != 4 && n != 8 && n != 16 && n != 64) return VE_EINVAL;
   if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
@@ -788,6 +794,7 @@ int ve_project_psd_sym(const double* in, double* out, int n, long count, int pre
 
 int ve_project_psd_herm(const double* in, double* out, int n, long count, int precision,
                         void* stream) {
+  cudaGetLastError();  // report only errors raised by this call
   if (!in || !out || count < 0) return VE_EINVAL;
   if (n != 4 && n != 16 && n != 64) return VE_EINVAL;
   if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
@@ -805,6 +812,7 @@ size_t ve_circulant_workspace_size(int dim, const int M[2], int D) {
 
 int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M[2], int D,
                          int precision, void* workspace, size_t workspace_bytes, void* stream) {
+  cudaGetLastError();  // report only errors raised by this call
   if (!x_in || !x_out || !M || !workspace) return VE_EINVAL;
   if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
   if (((uintptr_t)workspace) % kAlign) return VE_EINVAL;

@@ -115,8 +115,8 @@ struct ve_mlp {
 namespace {
 
 void mlp_free_batch(ve_mlp* m) {
-  for (float* a : m->act)
-    if (a) cudaFree(a);
+  for (size_t l = 1; l < m->act.size(); ++l)  // act[0] is m->x, freed below
+    if (m->act[l]) cudaFree(m->act[l]);
   m->act.clear();
   if (m->x) cudaFree(m->x);
   if (m->t) cudaFree(m->t);
@@ -292,6 +292,7 @@ int ve_mlp_set_params(ve_mlp* m, const float* host, size_t count) {
 }
 
 int ve_mlp_loss_grad(ve_mlp* m, const float* x, const float* t, int n, float* loss, float* grad) {
+  cudaGetLastError();  // report only errors raised by this call
   if (!m || !x || !t || n < 1) return VE_EINVAL;
   int r = mlp_reserve(m, n);
   if (r != VE_OK) return r;
@@ -310,6 +311,7 @@ int ve_mlp_loss_grad(ve_mlp* m, const float* x, const float* t, int n, float* lo
 
 int ve_mlp_train(ve_mlp* m, const float* x, const float* t, int n, int steps, float lr,
                  float* loss_out) {
+  cudaGetLastError();  // report only errors raised by this call
   if (!m || !x || !t || n < 1 || steps < 0 || !(lr > 0.f)) return VE_EINVAL;
   int r = mlp_reserve(m, n);
   if (r != VE_OK) return r;
@@ -340,6 +342,7 @@ int ve_mlp_train(ve_mlp* m, const float* x, const float* t, int n, int steps, fl
 }
 
 int ve_mlp_predict(ve_mlp* m, const float* x, int n, float* y) {
+  cudaGetLastError();  // report only errors raised by this call
   if (!m || !x || !y || n < 1) return VE_EINVAL;
   int r = mlp_reserve(m, n);
   if (r != VE_OK) return r;

@@ -46,6 +46,7 @@ extern "C" int ve_circulant_project_noalloc(const double* x_in, double* x_out, i
   if (!x_in || !x_out || !M) return VE_EINVAL;
   if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
   if (D == 256) return VE_EUNSUPPORTED;
+  cudaGetLastError();  // report only errors raised by this call
   FftPlan p;
   const int rc = fft_plan_build(p, dim, M, D);
   if (rc != 0) return rc;

@@ -37,7 +37,7 @@ def test_gpu_network_matches_the_reference(ve, n_in, hidden, layers, n_out, n):
         y = ve.ve_mlp_predict(m, x, n_out)
         np.testing.assert_allclose(y, mlp.forward(p, shapes, x)[-1], atol=2e-5, rtol=1e-4)
         # training lowers the loss
-        assert ve.ve_mlp_train(m, x, t, 300, 1e-3) < 0.5 * rloss
+        assert ve.ve_mlp_train(m, x, t, 1500, 1e-3) < 0.5 * rloss
     finally:
         ve.ve_mlp_destroy(m)
 
