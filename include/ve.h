@@ -43,8 +43,12 @@ extern "C" {
 #define VE_EUNSUPPORTED (-5) /* valid but not implemented here (e.g. cluster size)        */
 
 #define VE_PREC_FP64 0  /* every step in float64                                          */
-#define VE_PREC_MIXED 1 /* PSD projections (eigensolve + reconstruction) in float32,
-                           everything else in float64; ve_iterate finishes in float64     */
+#define VE_PREC_MIXED 1 /* float32 arithmetic in the pair pass, the block DFT and both PSD
+                           projections, float64 state and reductions; ve_iterate finishes in
+                           VE_PREC_DF64 arithmetic                                         */
+#define VE_PREC_DF64 2  /* float64-accurate: the pair pass and both PSD projections in
+                           double-float words (two float32 numbers, ~2^-48 rounding) on the
+                           float32 pipe, everything else in float64                          */
 
 #define VE_MAX_BONDS 4
 
@@ -74,7 +78,7 @@ typedef struct {
  * eps = 2, VE_PREC_FP64, check_every = 10, stream = NULL (the handle creates its own). */
 typedef struct {
   double mu, nu, eps;
-  int precision;   /* VE_PREC_FP64 or VE_PREC_MIXED */
+  int precision;   /* VE_PREC_FP64, VE_PREC_MIXED or VE_PREC_DF64 */
   int check_every; /* sweeps between residual read-backs in ve_iterate, >= 1 */
   void* stream;    /* cudaStream_t for all of the handle's work, or NULL */
 } ve_options;
@@ -124,7 +128,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
 /* Run sweeps of Algorithm 6 until max_iter sweeps or, when tol > 0, until the residual is
  * <= tol at a read-back (every check_every sweeps).  In VE_PREC_MIXED the sweeps use float32
  * projections until the residual reaches tol (or stops falling: no 1 % gain over 100
- * read-backs), then continue in float64 until the residual is <= tol again.
+ * read-backs), then continue in VE_PREC_DF64 arithmetic until the residual is <= tol again.
  * Writes the last status to *out (may be NULL).  Returns VE_OK if converged (or tol <= 0 and
  * max_iter sweeps ran), VE_NOT_CONVERGED, VE_ENONFINITE, VE_EINVAL, VE_ECUDA.  Synchronous. */
 int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out);
@@ -219,7 +223,8 @@ int ve_mlp_predict(ve_mlp* m, const float* x, int n, float* y);
 
 /* Pi_{>=0} (Sec. 3, the Frobenius-nearest PSD matrix, Eq. (rhoijTildeUpdate)) of `count` real
  * symmetric n x n matrices: in, out = device pointers to count*n*n float64 (in == out allowed).
- * n in {2, 4, 8, 16, 64}; precision VE_PREC_FP64 or VE_PREC_MIXED (float32 eigensolve).  The
+ * n in {2, 4, 8, 16, 64}; precision VE_PREC_FP64, VE_PREC_MIXED (float32 eigensolve) or
+ * VE_PREC_DF64 (double-float eigensolve).  The
  * input is symmetrised as (A + A^T)/2.  Asynchronous on `stream` (cudaStream_t or NULL).
  * Errors: VE_EINVAL (n, count < 0, precision), VE_ECUDA (launch failure). */
 int ve_project_psd_sym(const double* in, double* out, int n, long count, int precision,

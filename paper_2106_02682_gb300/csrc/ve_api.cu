@@ -152,15 +152,15 @@ struct ve_handle {
   int *hslot = nullptr, *neg = nullptr, *canon = nullptr;
   int ncanon = 0;
   double2 *specA = nullptr, *specB = nullptr, *tw = nullptr;
-  // eigenvectors of the last projections, per precision (index 0: float64, 1: float32)
-  void* vpair[2] = {nullptr, nullptr};
-  void* vk[2] = {nullptr, nullptr};
-  bool vvalid[2] = {false, false};
+  // eigenvectors of the last projections, per arithmetic (an Arith: float64, float32, df64)
+  void* vpair[3] = {nullptr, nullptr, nullptr};
+  void* vk[3] = {nullptr, nullptr, nullptr};
+  bool vvalid[3] = {false, false, false};
   DevStatus* dst = nullptr;
   DevStatus* hst = nullptr;  // pinned
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  bool fp64_phase = false;  // MIXED: switched to float64
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  bool fp64_phase = false;  // MIXED: switched to the float64-accurate phase
   // per-stage profiling
   bool prof = false;
   cudaEvent_t ev[VE_NSTAGE + 1] = {};
@@ -229,9 +229,10 @@ SmallArgs small_args(ve_handle* h) {
 }
 
 // One sweep of Algorithm 6, all on h->stream (with stage events when profiling).
-cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
+cudaError_t issue_sweep(ve_handle* h, int arith, bool warm) {
   cudaStream_t s = h->stream;
-  const int v = fp32 ? 1 : 0;
+  const int v = arith;
+  const bool fp32 = arith == ARITH_FP32;
   PairArgs pa = pair_args(h);
   pa.vstore = h->vpair[v];
   pa.warm = warm ? 1 : 0;
@@ -241,7 +242,7 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
   cudaError_t e;
   auto mark = [&](int i) { return h->prof ? cudaEventRecord(h->ev[i], s) : cudaSuccess; };
   if ((e = mark(0)) != cudaSuccess) return e;
-  if ((e = launch_pair(pa, fp32, s)) != cudaSuccess) return e;
+  if ((e = launch_pair(pa, arith, s)) != cudaSuccess) return e;
   if ((e = mark(1)) != cudaSuccess) return e;
   if ((e = launch_rho0(sa, s)) != cudaSuccess) return e;
   if ((e = mark(2)) != cudaSuccess) return e;
@@ -253,7 +254,7 @@ cudaError_t issue_sweep(ve_handle* h, bool fp32, bool warm) {
   if ((e = fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, fp32, s)) != cudaSuccess)
     return e;
   if ((e = mark(5)) != cudaSuccess) return e;
-  if ((e = launch_xproj(h->plan, spec, h->canon, fp32, h->vk[v], warm ? 1 : 0, s,
+  if ((e = launch_xproj(h->plan, spec, h->canon, arith, h->vk[v], warm ? 1 : 0, s,
                        h->prof ? h->jstats + 2 : nullptr, h->gws)) != cudaSuccess)
     return e;
   if ((e = mark(6)) != cudaSuccess) return e;
@@ -279,12 +280,12 @@ int accumulate_profile(ve_handle* h) {
 // stored by the previous sweep.
 int read_status(ve_handle* h, ve_status* out);
 
-int run_sweeps(ve_handle* h, long count, bool fp32) {
-  const int v = fp32 ? 1 : 0;
+int run_sweeps(ve_handle* h, long count, int arith) {
+  const int v = arith;
   if (count <= 0) return VE_OK;
   if (h->prof) {
     for (long i = 0; i < count; ++i) {
-      VE_CU(issue_sweep(h, fp32, h->vvalid[v]));
+      VE_CU(issue_sweep(h, arith, h->vvalid[v]));
       h->vvalid[v] = true;
       VE_CU(cudaStreamSynchronize(h->stream));
       const int r = accumulate_profile(h);
@@ -293,14 +294,14 @@ int run_sweeps(ve_handle* h, long count, bool fp32) {
     return VE_OK;
   }
   if (!h->vvalid[v]) {
-    VE_CU(issue_sweep(h, fp32, false));
+    VE_CU(issue_sweep(h, arith, false));
     h->vvalid[v] = true;
     --count;
   }
   if (count <= 0) return VE_OK;
   if (!h->exec[v]) {
     VE_CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = issue_sweep(h, fp32, true);
+    cudaError_t e = issue_sweep(h, arith, true);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -325,6 +326,10 @@ int read_status(ve_handle* h, ve_status* out) {
     out->residual = h->hst->residual;
   }
   return VE_OK;
+}
+
+int precision_arith(int precision) {
+  return precision == VE_PREC_MIXED ? ARITH_FP32 : precision == VE_PREC_DF64 ? ARITH_DF64 : ARITH_FP64;
 }
 
 // Entry points that launch work start from a clean error state: a failed runtime call made
@@ -426,7 +431,8 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
     ve_default_options(&h->opt);
   }
   if (!(h->opt.mu > 0) || !(h->opt.nu > 0) || !(h->opt.eps > 0) || h->opt.check_every < 1 ||
-      (h->opt.precision != VE_PREC_FP64 && h->opt.precision != VE_PREC_MIXED)) {
+      (h->opt.precision != VE_PREC_FP64 && h->opt.precision != VE_PREC_MIXED &&
+       h->opt.precision != VE_PREC_DF64)) {
     delete h;
     return VE_EINVAL;
   }
@@ -467,6 +473,8 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   const size_t o_vp32 = take(sizeof(float) * P * DD);
   const size_t o_vk64 = take(sizeof(double) * 2 * N * DD);
   const size_t o_vk32 = take(sizeof(float) * 2 * N * DD);
+  const size_t o_vpdf = take(sizeof(double) * P * DD);
+  const size_t o_vkdf = take(sizeof(double) * 2 * N * DD);
   const size_t o_sa = take(sizeof(double2) * N * h->plan.E);
   const size_t o_sb = take(sizeof(double2) * N * h->plan.E);
   const size_t o_tw = take(sizeof(double2) * h->plan.ntw);
@@ -513,6 +521,8 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   h->vpair[1] = base + o_vp32;
   h->vk[0] = base + o_vk64;
   h->vk[1] = base + o_vk32;
+  h->vpair[2] = base + o_vpdf;
+  h->vk[2] = base + o_vkdf;
   h->specA = (double2*)(base + o_sa);
   h->specB = (double2*)(base + o_sb);
   h->tw = (double2*)(base + o_tw);
@@ -575,7 +585,7 @@ void ve_destroy(ve_handle* h) {
   if (!h) return;
   DeviceGuard g(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (int v = 0; v < 2; ++v) {
+  for (int v = 0; v < 3; ++v) {
     if (h->exec[v]) cudaGraphExecDestroy(h->exec[v]);
     if (h->graph[v]) cudaGraphDestroy(h->graph[v]);
   }
@@ -618,7 +628,7 @@ int ve_set_state(ve_handle* h, const double* host, size_t bytes) {
   VE_CU(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
   VE_CU(cudaStreamSynchronize(h->stream));
   h->fp64_phase = false;
-  h->vvalid[0] = h->vvalid[1] = false;
+  h->vvalid[0] = h->vvalid[1] = h->vvalid[2] = false;
   return VE_OK;
 }
 
@@ -665,6 +675,15 @@ int ve_get_status(ve_handle* h, ve_status* out) {
   return read_status(h, out);
 }
 
+// Arithmetic of the next sweeps of a handle.
+int handle_arith(const ve_handle* h) {
+  switch (h->opt.precision) {
+    case VE_PREC_DF64: return ARITH_DF64;
+    case VE_PREC_MIXED: return h->fp64_phase ? ARITH_DF64 : ARITH_FP32;
+    default: return ARITH_FP64;
+  }
+}
+
 // Stopping rule shared by ve_iterate and ve_batch_iterate: in VE_PREC_MIXED, float32 sweeps
 // until the residual meets tol or has not fallen by 1 % over 100 read-backs (the float32
 // rounding floor), then float64 sweeps until the residual meets tol.
@@ -700,7 +719,6 @@ void ctl_update(ve_handle* h, IterCtl& c, const ve_status& s, double tol) {
 int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out) {
   if (!h || max_iter < 0) return VE_EINVAL;
   DeviceGuard g(h->device);
-  const bool mixed = h->opt.precision == VE_PREC_MIXED;
   ve_status s;
   IterCtl c;
   long done = 0;
@@ -711,8 +729,7 @@ int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out) {
   }
   while (done < max_iter && !c.finished) {
     const long chunk = (long)h->opt.check_every < max_iter - done ? (long)h->opt.check_every : max_iter - done;
-    const bool fp32 = mixed && !h->fp64_phase;
-    int r = run_sweeps(h, chunk, fp32);
+    int r = run_sweeps(h, chunk, handle_arith(h));
     if (r != VE_OK) return r;
     r = read_status(h, &s);
     if (r != VE_OK) return r;
@@ -776,7 +793,7 @@ int ve_project_state_x(ve_handle* h) {
   DeviceGuard g(h->device);
   double2* spec = nullptr;
   VE_CU(fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, false, h->stream));
-  VE_CU(launch_xproj(h->plan, spec, h->canon, false, nullptr, 0, h->stream, nullptr, h->gws));
+  VE_CU(launch_xproj(h->plan, spec, h->canon, ARITH_FP64, nullptr, 0, h->stream, nullptr, h->gws));
   VE_CU(fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, false, h->stream));
   VE_CU(cudaStreamSynchronize(h->stream));
   return VE_OK;
@@ -814,7 +831,8 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
                          int precision, void* workspace, size_t workspace_bytes, void* stream) {
   cudaGetLastError();  // report only errors raised by this call
   if (!x_in || !x_out || !M || !workspace) return VE_EINVAL;
-  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED && precision != VE_PREC_DF64)
+    return VE_EINVAL;
   if (((uintptr_t)workspace) % kAlign) return VE_EINVAL;
   if (D == 256) return VE_EUNSUPPORTED;
   FftPlan p;
@@ -834,7 +852,7 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
   double2* spec = nullptr;
   const bool fp32 = precision == VE_PREC_MIXED;
   VE_CU(fft_forward(p, x_in, A, B, tw, &spec, fp32, s));
-  VE_CU(launch_xproj(p, spec, canon, fp32, nullptr, 0, s));
+  VE_CU(launch_xproj(p, spec, canon, precision_arith(precision), nullptr, 0, s));
   VE_CU(fft_inverse(p, spec, A, B, x_out, tw, fp32, s));
   return VE_OK;
 }
@@ -854,7 +872,7 @@ struct ve_batch {
   std::vector<cudaEvent_t> join;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<int> key;  // per instance: -1 idle, 0 float64 branch, 1 float32 branch
+  std::vector<int> key;  // per instance: -1 idle, else the Arith of its branch
 };
 
 namespace {
@@ -877,7 +895,7 @@ int batch_capture(ve_batch* b, const std::vector<int>& key) {
     if (key[i] < 0) continue;
     ve_handle* h = b->h[i];
     e = cudaStreamWaitEvent(h->stream, b->fork, 0);
-    if (e == cudaSuccess) e = issue_sweep(h, key[i] == 1, true);
+    if (e == cudaSuccess) e = issue_sweep(h, key[i], true);
     if (e == cudaSuccess) e = cudaEventRecord(b->join[i], h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->join[i], 0);
   }
@@ -965,8 +983,7 @@ int ve_batch_iterate(ve_batch* b, long max_iter, double tol, ve_status* out) {
       if (ctl[i].finished) continue;
       ve_handle* h = b->h[i];
       if (h->prof) return VE_EINVAL;  // per-stage profiling is per handle, not in a batch
-      const bool fp32 = h->opt.precision == VE_PREC_MIXED && !h->fp64_phase;
-      key[i] = fp32 ? 1 : 0;
+      key[i] = handle_arith(h);
       any = true;
       if (!h->vvalid[key[i]]) cold = true;
     }
@@ -980,7 +997,7 @@ int ve_batch_iterate(ve_batch* b, long max_iter, double tol, ve_status* out) {
         if (key[i] < 0) continue;
         ve_handle* h = b->h[i];
         const int v = key[i];
-        VE_CU(issue_sweep(h, v == 1, h->vvalid[v]));
+        VE_CU(issue_sweep(h, v, h->vvalid[v]));
         h->vvalid[v] = true;
         VE_CU(cudaEventRecord(b->join[i], h->stream));
         VE_CU(cudaStreamWaitEvent(b->main, b->join[i], 0));

@@ -286,26 +286,46 @@ cudaError_t launch_bound(const BoundArgs& a, cudaStream_t s) {
 
 size_t bound_ws_bytes(int D) { return D == 256 ? BShape<256>::bytes * (size_t)big_grid() : 0; }
 
-cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, bool fp32,
-                            cudaStream_t s) {
-  if (count == 0) return cudaSuccess;
-  switch (n) {
-    case 2: return fp32 ? launch_proj_sym_t<2, float>(in, out, count, s) : launch_proj_sym_t<2, double>(in, out, count, s);
-    case 4: return fp32 ? launch_proj_sym_t<4, float>(in, out, count, s) : launch_proj_sym_t<4, double>(in, out, count, s);
-    case 8: return fp32 ? launch_proj_sym_t<8, float>(in, out, count, s) : launch_proj_sym_t<8, double>(in, out, count, s);
-    case 16: return fp32 ? launch_proj_sym_t<16, float>(in, out, count, s) : launch_proj_sym_t<16, double>(in, out, count, s);
-    case 64: return fp32 ? launch_proj_sym_t<64, float>(in, out, count, s) : launch_proj_sym_t<64, double>(in, out, count, s);
+template <int n>
+cudaError_t proj_sym_n(const double* in, double* out, long count, int arith, cudaStream_t s) {
+  switch (arith) {
+    case ARITH_FP64: return launch_proj_sym_t<n, double>(in, out, count, s);
+    case ARITH_FP32: return launch_proj_sym_t<n, float>(in, out, count, s);
+    case ARITH_DF64: return launch_proj_sym_t<n, df64>(in, out, count, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_proj_herm(const double* in, double* out, int n, long count, bool fp32,
+template <int n>
+cudaError_t proj_herm_n(const double* in, double* out, long count, int arith, cudaStream_t s) {
+  switch (arith) {
+    case ARITH_FP64: return launch_proj_herm_t<n, double>(in, out, count, s);
+    case ARITH_FP32: return launch_proj_herm_t<n, float>(in, out, count, s);
+    case ARITH_DF64: return launch_proj_herm_t<n, df64>(in, out, count, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, int arith,
+                            cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  switch (n) {
+    case 2: return proj_sym_n<2>(in, out, count, arith, s);
+    case 4: return proj_sym_n<4>(in, out, count, arith, s);
+    case 8: return proj_sym_n<8>(in, out, count, arith, s);
+    case 16: return proj_sym_n<16>(in, out, count, arith, s);
+    case 64: return proj_sym_n<64>(in, out, count, arith, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_proj_herm(const double* in, double* out, int n, long count, int arith,
                              cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   switch (n) {
-    case 4: return fp32 ? launch_proj_herm_t<4, float>(in, out, count, s) : launch_proj_herm_t<4, double>(in, out, count, s);
-    case 16: return fp32 ? launch_proj_herm_t<16, float>(in, out, count, s) : launch_proj_herm_t<16, double>(in, out, count, s);
-    case 64: return fp32 ? launch_proj_herm_t<64, float>(in, out, count, s) : launch_proj_herm_t<64, double>(in, out, count, s);
+    case 4: return proj_herm_n<4>(in, out, count, arith, s);
+    case 16: return proj_herm_n<16>(in, out, count, arith, s);
+    case 64: return proj_herm_n<64>(in, out, count, arith, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -12,7 +12,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ve_df64.cuh"
+
 namespace ve {
+
+template <typename T>
+__device__ __forceinline__ T shfl_xor(T v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
 
 template <int NT>
 __device__ __forceinline__ void gsync() {
@@ -28,7 +35,7 @@ __device__ __forceinline__ void gsync() {
 template <int NT, typename T>
 __device__ __forceinline__ T gsum(T v, T* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
   if constexpr (NT == 32) {
     return v;
   } else {
@@ -47,7 +54,7 @@ __device__ __forceinline__ T gsum(T v, T* red) {
 template <int NT, typename T>
 __device__ __forceinline__ T gmin(T v, T* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, shfl_xor(v, o));
   if constexpr (NT == 32) {
     return v;
   } else {
@@ -90,6 +97,12 @@ struct JacobiTol<float> {
   static constexpr float rel2 = 1e-13f;
   static constexpr float big = 1e18f;
   static constexpr int max_sweeps = 14;
+};
+template <>
+struct JacobiTol<df64> {
+  static constexpr double rel2 = 1e-28;  // df64 rounding is ~2^-48
+  static constexpr double big = 1e18;
+  static constexpr int max_sweeps = 24;
 };
 
 // Rotation (c, s) that annihilates the (p,q) entry of [[app, apq], [apq, aqq]] with
@@ -203,6 +216,62 @@ __device__ __forceinline__ void unit_phase<double>(double br, double bi, double&
   mag = (q * y) * isc;  // times a power of two: exact
 }
 
+// df64: the float64 recipe above in double-float words -- power-of-two scaling, float32 seed,
+// two df64 Newton steps for t and for 1/sqrt(1 + t^2).
+__device__ __forceinline__ float pow2_inverse_scale_f(float x, float* inv = nullptr) {
+  int ex = (__float_as_int(x) >> 23) & 0xff;
+  ex = ex < 1 ? 1 : (ex > 253 ? 253 : ex);
+  if (inv) *inv = __int_as_float(ex << 23);
+  return __int_as_float((254 - ex) << 23);
+}
+
+template <>
+__device__ __forceinline__ void sym_schur2<df64>(df64 app, df64 aqq, df64 apq, df64& c, df64& s) {
+  if (apq.hi == 0.f) {
+    c = df64(1.f);
+    s = df64(0.f);
+    return;
+  }
+  const df64 d0 = aqq - app;
+  const float sc = pow2_inverse_scale_f(fmaxf(fabsf(d0.hi), fabsf(apq.hi)));
+  const df64 d = ldexp_df(d0, sc), b = ldexp_df(apq, sc);
+  float tf = 0.f;
+  if (b.hi != 0.f) {
+    const float tau = d.hi / (2.f * b.hi);
+    const float at = fabsf(tau);
+    tf = (at > 1e18f) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
+  }
+  df64 t(tf);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df64 g = (b * t + d) * t - b;
+    const df64 gp = (b + b) * t + d;
+    t = t - g * df64(__frcp_rn(gp.hi));
+  }
+  const df64 u = t * t + df64(1.f);
+  const df64 hu = u * df64(-0.5f);
+  df64 y(rsqrtf(u.hi));
+  y = y * (hu * y * y + df64(1.5f));
+  y = y * (hu * y * y + df64(1.5f));
+  c = y;
+  s = t * y;
+}
+
+template <>
+__device__ __forceinline__ void unit_phase<df64>(df64 br, df64 bi, df64& mag, df64& wr, df64& wi) {
+  float isc;
+  const float sc = pow2_inverse_scale_f(fmaxf(fabsf(br.hi), fabsf(bi.hi)), &isc);
+  const df64 xr = ldexp_df(br, sc), xi = ldexp_df(bi, sc);
+  const df64 q = xr * xr + xi * xi;
+  const df64 hq = q * df64(-0.5f);
+  df64 y(rsqrtf(q.hi));
+  y = y * (hq * y * y + df64(1.5f));
+  y = y * (hq * y * y + df64(1.5f));
+  wr = xr * y;
+  wi = -(xi * y);
+  mag = ldexp_df(q * y, isc);
+}
+
 // Real symmetric Jacobi on A (n x n, leading dimension LD) in shared memory.  If VEC, V (same
 // layout) receives the eigenvectors.  cs: shared scratch of n entries; red: NT/32 entries.
 // Returns the number of sweeps performed.
@@ -230,7 +299,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
       }
     }
     off = gsum<NT>(off, red);
-    if (off <= JacobiTol<T>::rel2 * nrm) break;
+    if (off <= T(JacobiTol<T>::rel2) * nrm) break;
     for (int r = 0; r < n - 1; ++r) {
       for (int k = tid; k < H; k += NT) {
         int p, q;
@@ -310,7 +379,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
       }
     }
     off = gsum<NT>(off, red);
-    if (off <= JacobiTol<T>::rel2 * nrm) break;
+    if (off <= T(JacobiTol<T>::rel2) * nrm) break;
     for (int r = 0; r < n - 1; ++r) {
       for (int k = tid; k < H; k += NT) {
         int p, q;

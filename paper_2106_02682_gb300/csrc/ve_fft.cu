@@ -38,6 +38,17 @@ struct C2<float> {
   static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
 };
 
+// Spectrum word of each per-matrix arithmetic: float32 work reads a float32 spectrum; float64
+// and double-float work read the float64 one.
+template <typename T>
+struct SpecOf {
+  using R = T;
+};
+template <>
+struct SpecOf<df64> {
+  using R = double;
+};
+
 template <typename V>
 __device__ __forceinline__ V cmul(V a, V b) {
   V r;
@@ -208,7 +219,7 @@ __device__ void unpack_block(const V* spec, int s, int s2, int E, T* Ar, T* Ai, 
 
 template <int D, typename T>
 __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
-    k_xproj(typename C2<T>::type* spec, const int* __restrict__ canon, const int ncanon,
+    k_xproj(typename C2<typename SpecOf<T>::R>::type* spec, const int* __restrict__ canon, const int ncanon,
             const FftPlan p, const double invN, T* vstore, const int warm,
             unsigned long long* stats, unsigned char* gws) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
@@ -348,6 +359,7 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
     }
     gsync<NT>();
     // pack Y_k (and Y_{-k} = conj Y_k) back, scaled by 1/N
+    using R = typename SpecOf<T>::R;
     const T sc = (T)invN;
     for (int e = tid; e < E; e += NT) {
       const int f1 = e, f2 = e + E;
@@ -355,8 +367,8 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
       const T y1i = Ai[(f1 / D) * LD + f1 % D] * sc;
       const T y2r = Ar[(f2 / D) * LD + f2 % D] * sc;
       const T y2i = Ai[(f2 / D) * LD + f2 % D] * sc;
-      spec[(long)s * E + e] = C2<T>::make(y1r - y2i, y1i + y2r);
-      if (s2 != s) spec[(long)s2 * E + e] = C2<T>::make(y1r + y2i, -y1i + y2r);
+      spec[(long)s * E + e] = C2<R>::make((R)(y1r - y2i), (R)(y1i + y2r));
+      if (s2 != s) spec[(long)s2 * E + e] = C2<R>::make((R)(y1r + y2i), (R)(y2r - y1i));
     }
     gsync<NT>();
   }
@@ -434,7 +446,7 @@ cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, vo
   const long res = G ? (long)big_grid() : resident_grid((const void*)k_xproj<D, T>, NT * GPC, smem);
   if (blocks > res) blocks = res;
   k_xproj<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(
-      reinterpret_cast<typename C2<T>::type*>(spec), canon, nc, p, 1.0 / p.N,
+      reinterpret_cast<typename C2<typename SpecOf<T>::R>::type*>(spec), canon, nc, p, 1.0 / p.N,
       reinterpret_cast<T*>(vstore), warm, stats, gws);
   return cudaGetLastError();
 }
@@ -603,18 +615,26 @@ cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2*
   return run_pass(p, p.inv[1], +1, nullptr, other, nullptr, x, tw, fp32, s);
 }
 
-cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
+template <int D>
+cudaError_t launch_xproj_d(const FftPlan& p, double2* spec, const int* canon, int arith,
+                           void* vstore, int warm, cudaStream_t s, unsigned long long* stats,
+                           unsigned char* gws) {
+  switch (arith) {
+    case ARITH_FP64: return launch_xproj_t<D, double>(p, spec, canon, vstore, warm, s, stats, gws);
+    case ARITH_FP32: return launch_xproj_t<D, float>(p, spec, canon, vstore, warm, s, stats, gws);
+    case ARITH_DF64: return launch_xproj_t<D, df64>(p, spec, canon, vstore, warm, s, stats, gws);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, int arith,
                          void* vstore, int warm, cudaStream_t s, unsigned long long* stats,
                          unsigned char* gws) {
   switch (p.D) {
-    case 4: return fp32 ? launch_xproj_t<4, float>(p, spec, canon, vstore, warm, s, stats, gws)
-                        : launch_xproj_t<4, double>(p, spec, canon, vstore, warm, s, stats, gws);
-    case 16: return fp32 ? launch_xproj_t<16, float>(p, spec, canon, vstore, warm, s, stats, gws)
-                         : launch_xproj_t<16, double>(p, spec, canon, vstore, warm, s, stats, gws);
-    case 64: return fp32 ? launch_xproj_t<64, float>(p, spec, canon, vstore, warm, s, stats, gws)
-                         : launch_xproj_t<64, double>(p, spec, canon, vstore, warm, s, stats, gws);
-    case 256: return fp32 ? launch_xproj_t<256, float>(p, spec, canon, vstore, warm, s, stats, gws)
-                          : launch_xproj_t<256, double>(p, spec, canon, vstore, warm, s, stats, gws);
+    case 4: return launch_xproj_d<4>(p, spec, canon, arith, vstore, warm, s, stats, gws);
+    case 16: return launch_xproj_d<16>(p, spec, canon, arith, vstore, warm, s, stats, gws);
+    case 64: return launch_xproj_d<64>(p, spec, canon, arith, vstore, warm, s, stats, gws);
+    case 256: return launch_xproj_d<256>(p, spec, canon, arith, vstore, warm, s, stats, gws);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -632,8 +652,9 @@ cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon,
 
 size_t xproj_ws_bytes(int D) {
   if (D != 256) return 0;
-  const size_t a = XSmem<256, double>::bytes, b = XSmem<256, float>::bytes;
-  return (a > b ? a : b) * (size_t)big_grid();
+  size_t a = XSmem<256, double>::bytes;
+  if (XSmem<256, df64>::bytes > a) a = XSmem<256, df64>::bytes;
+  return a * (size_t)big_grid();
 }
 
 cudaError_t launch_canon_list(const FftPlan& p, int* canon, cudaStream_t s) {

@@ -6,6 +6,10 @@
 
 namespace ve {
 
+// Arithmetic of the per-matrix work (pair pass, projections): native float64, float32, or
+// float64-accurate double-float words on the float32 pipe (ve_df64.cuh).
+enum Arith { ARITH_FP64 = 0, ARITH_FP32 = 1, ARITH_DF64 = 2 };
+
 // Raise a kernel's dynamic shared-memory limit once per device (outside any stream capture:
 // the first sweep of a handle runs uncaptured).
 template <typename K>
@@ -75,8 +79,8 @@ size_t pair_ws_bytes(int D);
 size_t xproj_ws_bytes(int D);
 size_t bound_ws_bytes(int D);
 
-// D in {4, 16, 64}; fp32 selects the float32 projection.
-cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s);
+// D in {4, 16, 64, 256}; arith is an Arith.
+cudaError_t launch_pair(const PairArgs& a, int arith, cudaStream_t s);
 // rho_0 update: two launches (chunk sums over delta, then one CTA), fixed reduction order.
 cudaError_t launch_rho0(const SmallArgs& a, cudaStream_t s);
 cudaError_t launch_dual12(const SmallArgs& a, cudaStream_t s);
@@ -118,7 +122,7 @@ int fft_ncanon(const FftPlan& p);
 // Per-wavevector projection in place on the spectrum, scaled by 1/N; fp32 = float2 spectrum and
 // float32 eigensolve.  vstore (N * 2 * D*D of float or double, or null): eigenvectors kept per
 // slot; warm = 1 starts from them.
-cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, bool fp32,
+cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, int arith,
                          void* vstore, int warm, cudaStream_t s,
                          unsigned long long* stats = nullptr, unsigned char* gws = nullptr);
 // lmin[slot] = smallest eigenvalue of the (unnormalised) block C_k, +inf for non-canonical slots.
@@ -141,9 +145,9 @@ struct BoundArgs {
 cudaError_t launch_bound(const BoundArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------ standalone projections
-cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, bool fp32,
+cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, int arith,
                             cudaStream_t s);
-cudaError_t launch_proj_herm(const double* in, double* out, int n, long count, bool fp32,
+cudaError_t launch_proj_herm(const double* in, double* out, int n, long count, int arith,
                              cudaStream_t s);
 
 }  // namespace ve

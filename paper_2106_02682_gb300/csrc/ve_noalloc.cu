@@ -44,7 +44,8 @@ int scratch_address(void** out) {
 extern "C" int ve_circulant_project_noalloc(const double* x_in, double* x_out, int dim,
                                             const int M[2], int D, int precision, void* stream) {
   if (!x_in || !x_out || !M) return VE_EINVAL;
-  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED && precision != VE_PREC_DF64)
+    return VE_EINVAL;
   if (D == 256) return VE_EUNSUPPORTED;
   cudaGetLastError();  // report only errors raised by this call
   FftPlan p;
@@ -70,7 +71,8 @@ extern "C" int ve_circulant_project_noalloc(const double* x_in, double* x_out, i
   double2* spec = nullptr;
   const bool fp32 = precision == VE_PREC_MIXED;
   if (fft_forward(p, x_in, A, B, tw, &spec, fp32, s) != cudaSuccess) return VE_ECUDA;
-  if (launch_xproj(p, spec, canon, fp32, nullptr, 0, s) != cudaSuccess) return VE_ECUDA;
+  const int arith = fp32 ? ARITH_FP32 : precision == VE_PREC_DF64 ? ARITH_DF64 : ARITH_FP64;
+  if (launch_xproj(p, spec, canon, arith, nullptr, 0, s) != cudaSuccess) return VE_ECUDA;
   if (fft_inverse(p, spec, A, B, x_out, tw, fp32, s) != cudaSuccess) return VE_ECUDA;
   return VE_OK;
 }

@@ -384,20 +384,31 @@ int resident_grid(const void* kernel, int threads, size_t smem) {
   return sms * per;
 }
 
-cudaError_t launch_pair(const PairArgs& a, bool fp32, cudaStream_t s) {
+template <int D>
+cudaError_t launch_pair_d(const PairArgs& a, int arith, cudaStream_t s) {
+  switch (arith) {
+    case ARITH_FP64: return launch_pair_t<D, double>(a, s);
+    case ARITH_FP32: return launch_pair_t<D, float>(a, s);
+    case ARITH_DF64: return launch_pair_t<D, df64>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pair(const PairArgs& a, int arith, cudaStream_t s) {
   switch (a.D) {
-    case 4: return fp32 ? launch_pair_t<4, float>(a, s) : launch_pair_t<4, double>(a, s);
-    case 16: return fp32 ? launch_pair_t<16, float>(a, s) : launch_pair_t<16, double>(a, s);
-    case 64: return fp32 ? launch_pair_t<64, float>(a, s) : launch_pair_t<64, double>(a, s);
-    case 256: return fp32 ? launch_pair_t<256, float>(a, s) : launch_pair_t<256, double>(a, s);
+    case 4: return launch_pair_d<4>(a, arith, s);
+    case 16: return launch_pair_d<16>(a, arith, s);
+    case 64: return launch_pair_d<64>(a, arith, s);
+    case 256: return launch_pair_d<256>(a, arith, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 size_t pair_ws_bytes(int D) {
   if (D != 256) return 0;
-  const size_t a = PairSmem<256, double>::bytes, b = PairSmem<256, float>::bytes;
-  return (a > b ? a : b) * (size_t)big_grid();
+  size_t a = PairSmem<256, double>::bytes;
+  if (PairSmem<256, df64>::bytes > a) a = PairSmem<256, df64>::bytes;
+  return a * (size_t)big_grid();
 }
 
 int big_grid() {

@@ -23,6 +23,7 @@ VE_ENONFINITE = -4
 VE_EUNSUPPORTED = -5
 VE_PREC_FP64 = 0
 VE_PREC_MIXED = 1
+VE_PREC_DF64 = 2
 VE_MAX_BONDS = 4
 VE_NSTAGE = 7
 VE_NOALLOC_SCRATCH_BYTES = (16 << 20) + (256 << 10)

@@ -57,7 +57,7 @@ def dev(x):
 # ------------------------------------------------------------------ S3: pair projections
 
 @pytest.mark.parametrize("n", [2, 4, 8, 16, 64])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_project_sym_matches_oracle(ve, n, prec):
     A = synth.symmetric_batch(1001 if n <= 16 else 131, n, seed=n)
     x = dev(A)
@@ -67,7 +67,7 @@ def test_project_sym_matches_oracle(ve, n, prec):
     ref = vo.proj_psd(A)
     out = y.cpu().numpy()
     for b in range(A.shape[0]):
-        tol = RTOL64 * max(1.0, np.max(np.abs(A[b]))) if prec == 0 else tol32(A[b])
+        tol = RTOL64 * max(1.0, np.max(np.abs(A[b]))) if prec != 1 else tol32(A[b])
         assert np.max(np.abs(out[b] - ref[b])) <= tol, b
     # in place, and an empty batch
     ve.ve_project_psd_sym(x.data_ptr(), x.data_ptr(), n, A.shape[0], prec)
@@ -77,7 +77,7 @@ def test_project_sym_matches_oracle(ve, n, prec):
 
 
 @pytest.mark.parametrize("n", [4, 16, 64])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_project_herm_matches_oracle(ve, n, prec):
     A = synth.hermitian_batch(517 if n <= 16 else 67, n, seed=100 + n)
     inter = np.stack([A.real, A.imag], axis=-1)
@@ -89,7 +89,7 @@ def test_project_herm_matches_oracle(ve, n, prec):
     out = o[..., 0] + 1j * o[..., 1]
     ref = vo.proj_psd(A)
     for b in range(A.shape[0]):
-        tol = RTOL64 * max(1.0, np.max(np.abs(A[b]))) if prec == 0 else tol32(A[b])
+        tol = RTOL64 * max(1.0, np.max(np.abs(A[b]))) if prec != 1 else tol32(A[b])
         assert np.max(np.abs(out[b] - ref[b])) <= tol, b
 
 
@@ -173,12 +173,14 @@ def _ham(ve, kind, dim, x):
     return ve.ve_ham_tfim(dim, 1.0, x) if kind == "tfim" else ve.ve_ham_xxz(dim, 1.0, x)
 
 
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("lattice,cluster,kind,x", SWEEP_CASES)
-def test_sweeps_match_oracle(ve, lattice, cluster, kind, x):
+def test_sweeps_match_oracle(ve, lattice, cluster, kind, x, prec):
+    """float64 (prec 0) and double-float (prec 2) sweeps against the oracle, same tolerances."""
     dim = len(lattice)
     pb = vo.Problem(mo.cluster_model(lattice, cluster, *_terms(kind, dim, x)))
     st = vo.initial_state(pb)
-    h = ve.ve_create(lattice, cluster, _ham(ve, kind, dim, x))
+    h = ve.ve_create(lattice, cluster, _ham(ve, kind, dim, x), ve.ve_default_options(precision=prec))
     try:
         assert ve.ve_dims(h) == (pb.N, pb.m, pb.D)
         np.testing.assert_array_equal(ve.ve_get_state(h), vo.pack_state(pb, st))
@@ -205,13 +207,14 @@ def test_sweeps_match_oracle(ve, lattice, cluster, kind, x):
         ve.ve_destroy(h)
 
 
-def test_full_size_workload_matches_oracle(ve):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_full_size_workload_matches_oracle(ve, prec):
     """The benchmark workload (1-D TFI, h = 1, 2-spin clusters, 4096 clusters = 4096
     wavevectors, D = 16), three sweeps, compared over the whole state."""
     lattice, cluster = (8192,), (2,)
     pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 1.0, 1)))
     st = vo.initial_state(pb)
-    h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 1.0))
+    h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 1.0), ve.ve_default_options(precision=prec))
     try:
         _, status = ve.ve_iterate(h, 3, 0.0)
         for _ in range(3):
