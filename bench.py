@@ -6,7 +6,7 @@ instance (pair pass, rho_0 update, dual updates, block DFT, per-wavevector proje
 DFT).  Default workload: 1-D transverse-field Ising chain, h = 1, 2-spin clusters (16 x 16 pair
 marginals), 4096 clusters = 4096 wavevectors (8192 spins), float64.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|df64|mixed]
                     [--workload NAME] [--impl ours|reference] [--no-ttb]
 
 Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank runs its own replica of the
@@ -334,7 +334,7 @@ def run_ours(args):
         if not args.no_ttb and rank == 0:
             batch = batch_rate(ve, synth, "paper", 64, 200, ve.VE_PREC_FP64)
 
-        # ---- time to certified bound, float64 and mixed, fresh handles
+        # ---- time to certified bound in each precision mode, fresh handles
         ttb = None
         if not args.no_ttb and rank == 0:
             tw_ = synth.WORKLOADS[args.ttb_workload]
@@ -342,7 +342,8 @@ def run_ours(args):
             tham = (ve.ve_ham_tfim(tdim, 1.0, tw_["h"]) if tw_["kind"] == "tfim"
                     else ve.ve_ham_xxz(tdim, 1.0, tw_["h"]))
             ttb = {"workload": args.ttb_workload, "tol": 1e-6}
-            for pname, pcode in (("fp64", ve.VE_PREC_FP64), ("mixed", ve.VE_PREC_MIXED)):
+            for pname, pcode in (("fp64", ve.VE_PREC_FP64), ("df64", ve.VE_PREC_DF64),
+                                 ("mixed", ve.VE_PREC_MIXED)):
                 hh = ve.ve_create(tw_["lattice"], tw_["cluster"], tham,
                                   ve.ve_default_options(precision=pcode, stream=stream.cuda_stream))
                 try:

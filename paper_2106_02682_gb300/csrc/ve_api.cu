@@ -804,8 +804,9 @@ int ve_project_psd_sym(const double* in, double* out, int n, long count, int pre
   cudaGetLastError();  // report only errors raised by this call
   if (!in || !out || count < 0) return VE_EINVAL;
   if (n != 2 && n != 4 && n != 8 && n != 16 && n != 64) return VE_EINVAL;
-  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
-  VE_CU(launch_proj_sym(in, out, n, count, precision == VE_PREC_MIXED, (cudaStream_t)stream));
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED && precision != VE_PREC_DF64)
+    return VE_EINVAL;
+  VE_CU(launch_proj_sym(in, out, n, count, precision_arith(precision), (cudaStream_t)stream));
   return VE_OK;
 }
 
@@ -814,8 +815,9 @@ int ve_project_psd_herm(const double* in, double* out, int n, long count, int pr
   cudaGetLastError();  // report only errors raised by this call
   if (!in || !out || count < 0) return VE_EINVAL;
   if (n != 4 && n != 16 && n != 64) return VE_EINVAL;
-  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED) return VE_EINVAL;
-  VE_CU(launch_proj_herm(in, out, n, count, precision == VE_PREC_MIXED, (cudaStream_t)stream));
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED && precision != VE_PREC_DF64)
+    return VE_EINVAL;
+  VE_CU(launch_proj_herm(in, out, n, count, precision_arith(precision), (cudaStream_t)stream));
   return VE_OK;
 }
 

@@ -5,7 +5,10 @@
 // A "group" is NT threads that own one matrix: one warp (NT = 32) for n <= 16, the whole CTA
 // (NT = 256) for n = 64.  The Jacobi sweep uses the round-robin (circle) ordering: n - 1
 // rounds per sweep, n/2 disjoint index pairs per round, so all rotations of a round commute
-// and the two-sided update splits into independent 2x2 blocks (one per pair of pairs).
+// and the two-sided update splits into independent 2x2 blocks (one per pair of pairs).  A
+// pair's own block becomes diagonal in closed form; of the other blocks only those above the
+// diagonal are transformed, their mirror images are stored as (conjugate) transposes, so A
+// stays exactly symmetric and a round costs half the flops of the full two-sided update.
 // Eigenvalues end on the diagonal of A, eigenvectors in the columns of V.
 #pragma once
 
@@ -117,19 +120,24 @@ struct JacobiTol<df64> {
 // 2 b t + d never falls below max(|d|, 2|b|) >= 1 near the root), and c by two Newton steps of
 // the reciprocal square root seeded in float32.  c^2 + s^2 = 1 to float64 rounding, which is
 // what keeps the accumulated eigenvectors orthogonal.
+//
+// The tangent is returned too: the rotated diagonal is app - t apq, aqq + t apq (the root
+// condition turns c^2 app - 2 c s apq + s^2 aqq into app - t apq).
 template <typename T>
-__device__ __forceinline__ void sym_schur2(T app, T aqq, T apq, T& c, T& s);
+__device__ __forceinline__ void sym_schur2(T app, T aqq, T apq, T& c, T& s, T& t);
 
 template <>
-__device__ __forceinline__ void sym_schur2<float>(float app, float aqq, float apq, float& c, float& s) {
+__device__ __forceinline__ void sym_schur2<float>(float app, float aqq, float apq, float& c, float& s,
+                                                  float& t) {
   if (apq == 0.f) {
     c = 1.f;
     s = 0.f;
+    t = 0.f;
     return;
   }
   const float tau = (aqq - app) / (2.f * apq);
   const float at = fabsf(tau);
-  const float t = (at > JacobiTol<float>::big) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
+  t = (at > JacobiTol<float>::big) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
   const float u = fmaf(t, t, 1.f);  // in [1, 2]
   float y = rsqrtf(u);
   y = y * fmaf(-0.5f * u, y * y, 1.5f);  // one Newton step: c^2 + s^2 = 1 to float rounding
@@ -148,10 +156,11 @@ __device__ __forceinline__ double pow2_inverse_scale(double x, double* inv = nul
 
 template <>
 __device__ __forceinline__ void sym_schur2<double>(double app, double aqq, double apq, double& c,
-                                                   double& s) {
+                                                   double& s, double& t) {
   if (apq == 0.0) {
     c = 1.0;
     s = 0.0;
+    t = 0.0;
     return;
   }
   const double d0 = aqq - app;
@@ -164,7 +173,7 @@ __device__ __forceinline__ void sym_schur2<double>(double app, double aqq, doubl
     const float at = fabsf(tau);
     tf = (at > 1e18f) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
   }
-  double t = (double)tf;
+  t = (double)tf;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const double g = fma(fma(b, t, d), t, -b);
@@ -226,10 +235,12 @@ __device__ __forceinline__ float pow2_inverse_scale_f(float x, float* inv = null
 }
 
 template <>
-__device__ __forceinline__ void sym_schur2<df64>(df64 app, df64 aqq, df64 apq, df64& c, df64& s) {
+__device__ __forceinline__ void sym_schur2<df64>(df64 app, df64 aqq, df64 apq, df64& c, df64& s,
+                                                 df64& t) {
   if (apq.hi == 0.f) {
     c = df64(1.f);
     s = df64(0.f);
+    t = df64(0.f);
     return;
   }
   const df64 d0 = aqq - app;
@@ -241,7 +252,7 @@ __device__ __forceinline__ void sym_schur2<df64>(df64 app, df64 aqq, df64 apq, d
     const float at = fabsf(tau);
     tf = (at > 1e18f) ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
   }
-  df64 t(tf);
+  t = df64(tf);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const df64 g = (b * t + d) * t - b;
@@ -277,6 +288,7 @@ __device__ __forceinline__ void unit_phase<df64>(df64 br, df64 bi, df64& mag, df
 // Returns the number of sweeps performed.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
 __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
+  static_assert(n == 2 || n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
@@ -301,33 +313,45 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
     off = gsum<NT>(off, red);
     if (off <= T(JacobiTol<T>::rel2) * nrm) break;
     for (int r = 0; r < n - 1; ++r) {
+      // the rotation of each pair, and the pair's own 2x2 block made diagonal
       for (int k = tid; k < H; k += NT) {
         int p, q;
         rr_pair(n, r, k, p, q);
-        T c, s;
-        sym_schur2<T>(A[p * LD + p], A[q * LD + q], A[p * LD + q], c, s);
+        const T app = A[p * LD + p], aqq = A[q * LD + q], apq = A[p * LD + q];
+        T c, s, t;
+        sym_schur2<T>(app, aqq, apq, c, s, t);
         cs[k] = c;
         cs[H + k] = s;
+        A[p * LD + p] = app - t * apq;
+        A[q * LD + q] = aqq + t * apq;
+        A[p * LD + q] = T(0);
+        A[q * LD + p] = T(0);
       }
       gsync<NT>();
-      for (int b = tid; b < H * H; b += NT) {
-        const int k1 = b / H, k2 = b % H;
-        int p1, q1, p2, q2;
-        rr_pair(n, r, k1, p1, q1);
-        rr_pair(n, r, k2, p2, q2);
-        const T c1 = cs[k1], s1 = cs[H + k1], c2 = cs[k2], s2 = cs[H + k2];
-        const T m11 = A[p1 * LD + p2], m12 = A[p1 * LD + q2];
-        const T m21 = A[q1 * LD + p2], m22 = A[q1 * LD + q2];
-        const T x11 = c2 * m11 - s2 * m12, x12 = s2 * m11 + c2 * m12;
-        const T x21 = c2 * m21 - s2 * m22, x22 = s2 * m21 + c2 * m22;
-        A[p1 * LD + p2] = c1 * x11 - s1 * x21;
-        A[q1 * LD + q2] = s1 * x12 + c1 * x22;
-        if (k1 == k2) {
-          A[p1 * LD + q2] = T(0);
-          A[q1 * LD + p2] = T(0);
-        } else {
-          A[p1 * LD + q2] = c1 * x12 - s1 * x22;
-          A[q1 * LD + p2] = s1 * x11 + c1 * x21;
+      if constexpr (H >= 2) {
+        // the blocks (k1, k2), k1 < k2 -- enumerated as the pairs of a circle ordering of the
+        // H pair indices -- and their transposes (k2, k1)
+        for (int b = tid; b < H * (H - 1) / 2; b += NT) {
+          int k1, k2;
+          rr_pair(H, b / (H / 2), b % (H / 2), k1, k2);
+          int p1, q1, p2, q2;
+          rr_pair(n, r, k1, p1, q1);
+          rr_pair(n, r, k2, p2, q2);
+          const T c1 = cs[k1], s1 = cs[H + k1], c2 = cs[k2], s2 = cs[H + k2];
+          const T m11 = A[p1 * LD + p2], m12 = A[p1 * LD + q2];
+          const T m21 = A[q1 * LD + p2], m22 = A[q1 * LD + q2];
+          const T x11 = c2 * m11 - s2 * m12, x12 = s2 * m11 + c2 * m12;
+          const T x21 = c2 * m21 - s2 * m22, x22 = s2 * m21 + c2 * m22;
+          const T y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+          const T y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+          A[p1 * LD + p2] = y11;
+          A[p2 * LD + p1] = y11;
+          A[p1 * LD + q2] = y12;
+          A[q2 * LD + p1] = y12;
+          A[q1 * LD + p2] = y21;
+          A[p2 * LD + q1] = y21;
+          A[q1 * LD + q2] = y22;
+          A[q2 * LD + q1] = y22;
         }
       }
       if constexpr (VEC) {
@@ -353,6 +377,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
 // Returns the number of sweeps performed.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
 __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
+  static_assert(n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
@@ -381,21 +406,34 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
     off = gsum<NT>(off, red);
     if (off <= T(JacobiTol<T>::rel2) * nrm) break;
     for (int r = 0; r < n - 1; ++r) {
+      // the rotation of each pair, and the pair's own 2x2 block made (real) diagonal
       for (int k = tid; k < H; k += NT) {
         int p, q;
         rr_pair(n, r, k, p, q);
+        const T app = Ar[p * LD + p], aqq = Ar[q * LD + q];
         const T br = Ar[p * LD + q], bi = Ai[p * LD + q];
-        T c, s, mag = T(0), wr = T(1), wi = T(0);
+        T c, s, t, mag = T(0), wr = T(1), wi = T(0);
         if (br != T(0) || bi != T(0)) unit_phase<T>(br, bi, mag, wr, wi);
-        sym_schur2<T>(Ar[p * LD + p], Ar[q * LD + q], mag, c, s);
+        sym_schur2<T>(app, aqq, mag, c, s, t);
         cs[k] = c;
         cs[H + k] = s;
         cs[2 * H + k] = wr;
         cs[3 * H + k] = wi;
+        Ar[p * LD + p] = app - t * mag;
+        Ar[q * LD + q] = aqq + t * mag;
+        Ai[p * LD + p] = T(0);
+        Ai[q * LD + q] = T(0);
+        Ar[p * LD + q] = T(0);
+        Ai[p * LD + q] = T(0);
+        Ar[q * LD + p] = T(0);
+        Ai[q * LD + p] = T(0);
       }
       gsync<NT>();
-      for (int b = tid; b < H * H; b += NT) {
-        const int k1 = b / H, k2 = b % H;
+      // the blocks (k1, k2), k1 < k2 (pairs of a circle ordering of the H pair indices), and
+      // their conjugate transposes (k2, k1)
+      for (int b = tid; b < H * (H - 1) / 2; b += NT) {
+        int k1, k2;
+        rr_pair(H, b / (H / 2), b % (H / 2), k1, k2);
         int p1, q1, p2, q2;
         rr_pair(n, r, k1, p1, q1);
         rr_pair(n, r, k2, p2, q2);
@@ -421,29 +459,26 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
         const T y11i = c1 * x11i - (sw1r * x21i + sw1i * x21r);
         const T y22r = s1 * x12r + (cw1r * x22r - cw1i * x22i);
         const T y22i = s1 * x12i + (cw1r * x22i + cw1i * x22r);
-        if (k1 == k2) {
-          Ar[p1 * LD + p2] = y11r;
-          Ai[p1 * LD + p2] = T(0);
-          Ar[q1 * LD + q2] = y22r;
-          Ai[q1 * LD + q2] = T(0);
-          Ar[p1 * LD + q2] = T(0);
-          Ai[p1 * LD + q2] = T(0);
-          Ar[q1 * LD + p2] = T(0);
-          Ai[q1 * LD + p2] = T(0);
-        } else {
-          const T y12r = c1 * x12r - (sw1r * x22r - sw1i * x22i);
-          const T y12i = c1 * x12i - (sw1r * x22i + sw1i * x22r);
-          const T y21r = s1 * x11r + (cw1r * x21r - cw1i * x21i);
-          const T y21i = s1 * x11i + (cw1r * x21i + cw1i * x21r);
-          Ar[p1 * LD + p2] = y11r;
-          Ai[p1 * LD + p2] = y11i;
-          Ar[q1 * LD + q2] = y22r;
-          Ai[q1 * LD + q2] = y22i;
-          Ar[p1 * LD + q2] = y12r;
-          Ai[p1 * LD + q2] = y12i;
-          Ar[q1 * LD + p2] = y21r;
-          Ai[q1 * LD + p2] = y21i;
-        }
+        const T y12r = c1 * x12r - (sw1r * x22r - sw1i * x22i);
+        const T y12i = c1 * x12i - (sw1r * x22i + sw1i * x22r);
+        const T y21r = s1 * x11r + (cw1r * x21r - cw1i * x21i);
+        const T y21i = s1 * x11i + (cw1r * x21i + cw1i * x21r);
+        Ar[p1 * LD + p2] = y11r;
+        Ai[p1 * LD + p2] = y11i;
+        Ar[p2 * LD + p1] = y11r;
+        Ai[p2 * LD + p1] = -y11i;
+        Ar[q1 * LD + q2] = y22r;
+        Ai[q1 * LD + q2] = y22i;
+        Ar[q2 * LD + q1] = y22r;
+        Ai[q2 * LD + q1] = -y22i;
+        Ar[p1 * LD + q2] = y12r;
+        Ai[p1 * LD + q2] = y12i;
+        Ar[q2 * LD + p1] = y12r;
+        Ai[q2 * LD + p1] = -y12i;
+        Ar[q1 * LD + p2] = y21r;
+        Ai[q1 * LD + p2] = y21i;
+        Ar[p2 * LD + q1] = y21r;
+        Ai[p2 * LD + q1] = -y21i;
       }
       if constexpr (VEC) {
         for (int t = tid; t < n * H; t += NT) {
