@@ -146,7 +146,18 @@ int ve_dims(const ve_handle* h, int* N, int* m, int* D);
 /* Packed state: rho_0 (m^2), rho~ (P D^2), Lambda (P D^2), Lambda1 (P m^2), Lambda2 (P m^2),
  * X (N D^2), P = N - 1, float64, each block row-major.  ve_state_size gives the byte count;
  * get/set copy through `host` (host memory, bytes must equal that size; VE_EINVAL otherwise).
- * ve_set_state clears the stored previous energy, so the next d_energy is +inf. */
+ * ve_set_state clears the stored previous energy, so the next d_energy is +inf.
+ *
+ * Opposite offsets delta and -delta describe the same pairs of clusters seen from either end,
+ * and a sweep commutes with exchanging the two clusters of a pair.  A sweep therefore updates,
+ * of each pair {delta, -delta} (delta != -delta), only the member with the smaller linear index
+ * and writes the other as its swap image: rho~ and Lambda conjugated by the factor exchange,
+ * Lambda1 and Lambda2 exchanged, X' transposed.  Every state the solver produces from
+ * ve_create's initial state has this symmetry (X up to rounding); a state set here without it
+ * takes it from those members in its first sweep.  An offset with -delta = delta is updated on
+ * its own; the X step needs its X' block symmetric (the wavevector blocks Hermitian), which
+ * holds when that offset's rho~, Lambda are swap-symmetric and its Lambda1 = Lambda2, as in
+ * every state the solver produces. */
 size_t ve_state_size(const ve_handle* h);
 int ve_get_state(ve_handle* h, double* host, size_t bytes);
 int ve_set_state(ve_handle* h, const double* host, size_t bytes);

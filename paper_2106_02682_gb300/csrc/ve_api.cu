@@ -131,6 +131,27 @@ int build_model(const ve_lattice* lat, const ve_cluster* clu, const ve_hamiltoni
   return VE_OK;
 }
 
+// True when H_{0,-delta} = S H_{0,delta} S for every offset, S the exchange of the two
+// clusters' factors.  build_model places every bond in both blocks this way, so this holds up
+// to the order in which bond terms were added; it is what lets a sweep update one member of
+// each pair {delta, -delta} and write the other as its swap image.
+bool model_swap_symmetric(const Model& md) {
+  const int m = md.m, D = md.D;
+  double scale = 0.0;
+  for (const auto& kv : md.pair)
+    for (double x : kv.second) scale = fmax(scale, fabs(x));
+  for (const auto& kv : md.pair) {
+    const auto it = md.pair.find(md.neg[kv.first]);
+    for (int e = 0; e < D * D; ++e) {
+      const int i = e / D, j = e % D;
+      const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+      const double img = it == md.pair.end() ? 0.0 : it->second[(size_t)(pb * m + pa) * D + (pd * m + pc)];
+      if (fabs(kv.second[e] - img) > 1e-13 * (1.0 + scale)) return false;
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 struct ve_handle {
@@ -151,6 +172,9 @@ struct ve_handle {
          *H0 = nullptr, *lmin_pairs = nullptr, *lmin_k = nullptr, *lmin0 = nullptr;
   int *hslot = nullptr, *neg = nullptr, *canon = nullptr;
   int ncanon = 0;
+  // pair offsets tied to their opposite (k_pair, k_dual12): Pc work items
+  int Pc = 0;
+  int *pidx = nullptr, *pmir = nullptr, *ptie = nullptr;
   double2 *specA = nullptr, *specB = nullptr, *tw = nullptr;
   // eigenvectors of the last projections, per arithmetic (an Arith: float64, float32, df64)
   void* vpair[3] = {nullptr, nullptr, nullptr};
@@ -201,6 +225,9 @@ PairArgs pair_args(ve_handle* h) {
   a.part = h->part;
   a.vstore = nullptr;
   a.warm = 0;
+  a.Pc = h->Pc;
+  a.pidx = h->pidx;
+  a.pmir = h->pmir;
   return a;
 }
 
@@ -225,6 +252,7 @@ SmallArgs small_args(ve_handle* h) {
   a.part2 = h->part2;
   a.st = h->dst;
   a.rho0_partial = h->rho0_partial;
+  a.ptie = h->ptie;
   return a;
 }
 
@@ -469,6 +497,9 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   const size_t o_hslot = take(sizeof(int) * N);
   const size_t o_neg = take(sizeof(int) * N);
   const size_t o_canon = take(sizeof(int) * N);
+  const size_t o_pidx = take(sizeof(int) * P);
+  const size_t o_pmir = take(sizeof(int) * P);
+  const size_t o_ptie = take(sizeof(int) * P);
   const size_t o_vp64 = take(sizeof(double) * P * DD);
   const size_t o_vp32 = take(sizeof(float) * P * DD);
   const size_t o_vk64 = take(sizeof(double) * 2 * N * DD);
@@ -516,6 +547,9 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   h->hslot = (int*)(base + o_hslot);
   h->neg = (int*)(base + o_neg);
   h->canon = (int*)(base + o_canon);
+  h->pidx = (int*)(base + o_pidx);
+  h->pmir = (int*)(base + o_pmir);
+  h->ptie = (int*)(base + o_ptie);
   h->ncanon = fft_ncanon(h->plan);
   h->vpair[0] = base + o_vp64;
   h->vpair[1] = base + o_vp32;
@@ -553,6 +587,19 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
     memcpy(hb.data() + (size_t)k * DD, kv.second.data(), sizeof(double) * DD);
     ++k;
   }
+  // work items of the pair pass: the canonical (smaller linear index) member of each pair of
+  // opposite offsets, with the other as its image; every offset on its own if H is not tied
+  std::vector<int> pidx, pmir, ptie(P, -2);
+  const bool tied = model_swap_symmetric(md);
+  for (int dl = 1; dl < N; ++dl) {
+    const int nd = md.neg[dl];
+    if (tied && nd < dl) continue;
+    const int img = (!tied || nd == dl) ? -1 : nd - 1;
+    pidx.push_back(dl - 1);
+    pmir.push_back(img);
+    ptie[dl - 1] = img;
+  }
+  h->Pc = (int)pidx.size();
   DevStatus ds;
   memset(&ds, 0, sizeof(ds));
   ds.e_prev = NAN;
@@ -566,6 +613,9 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->H0, md.H0.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->hslot, hslot.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->neg, md.neg.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pidx, pidx.data(), sizeof(int) * h->Pc, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pmir, pmir.data(), sizeof(int) * h->Pc, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->ptie, ptie.data(), sizeof(int) * P, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->dst, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_fft_tables(h->plan, h->tw, h->stream);
   if (e == cudaSuccess) e = launch_canon_list(h->plan, h->canon, h->stream);

@@ -27,7 +27,7 @@ struct BShape {
 };
 
 template <int D>
-__global__ void __launch_bounds__(BShape<D>::NT * BShape<D>::GPC) k_bound_pairs(const BoundArgs a) {
+__global__ void __launch_bounds__(BShape<D>::NT * BShape<D>::GPC, GroupShape<D>::MINB) k_bound_pairs(const BoundArgs a) {
   constexpr int m = BShape<D>::m, NT = BShape<D>::NT, LD = BShape<D>::LD, GPC = BShape<D>::GPC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;

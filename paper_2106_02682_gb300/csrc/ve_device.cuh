@@ -511,7 +511,11 @@ struct GroupShape {
   static constexpr int NT = (n <= 16) ? 32 : (n <= 64 ? 256 : 512);
   static constexpr int LD = n + 1;
   static constexpr bool GLOBAL = n > 64;
-  static constexpr int GPC = (NT == 32) ? 4 : 1;  // groups per CTA
+  // One group per CTA: a batch of a few thousand warp-sized groups then spreads over the SMs
+  // to within one group (four-warp CTAs left a quarter of the SMs a whole CTA short).
+  static constexpr int GPC = 1;
+  // resident CTAs per SM the register budget must allow: at most 128 registers a thread
+  static constexpr int MINB = (NT == 32) ? 16 : (NT == 256 ? 2 : 1);
 };
 
 // m = sqrt(D) for the pair dimension D = m^2 of a cluster of dimension m.

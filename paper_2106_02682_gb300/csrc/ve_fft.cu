@@ -218,7 +218,7 @@ __device__ void unpack_block(const V* spec, int s, int s2, int E, T* Ar, T* Ai, 
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
+__global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupShape<D>::MINB)
     k_xproj(typename C2<typename SpecOf<T>::R>::type* spec, const int* __restrict__ canon, const int ncanon,
             const FftPlan p, const double invN, T* vstore, const int warm,
             unsigned long long* stats, unsigned char* gws) {
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256) k_canon_list(const FftPlan p, int* canon)
 }
 
 template <int D>
-__global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC)
+__global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupShape<D>::MINB)
     k_xeig(const double2* spec, const int* __restrict__ canon, const int ncanon, const FftPlan p,
            double* lmin, unsigned char* gws) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;

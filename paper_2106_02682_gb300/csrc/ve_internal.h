@@ -32,8 +32,8 @@ struct PairArgs {
   const double* rho0;   // m*m
   double* rt;           // P*D*D   rho~ (read, then overwritten)
   double* lam;          // P*D*D   Lambda
-  const double* lam1;   // P*m*m
-  const double* lam2;   // P*m*m
+  double* lam1;         // P*m*m   (read; the images of tied offsets are written)
+  double* lam2;         // P*m*m
   double* X;            // N*D*D   X_{0,delta}; blocks 1..N-1 become X' in the pair pass
   const double* hb;     // nonzero pair Hamiltonian blocks, D*D each
   const int* hslot;     // per linear delta: index into hb or -1
@@ -44,6 +44,12 @@ struct PairArgs {
   int warm;             // 1: start each Jacobi from V^T C V with the stored V
   unsigned long long* stats;  // null, or [0] += Jacobi sweeps, [1] += matrices (profiling)
   unsigned char* gws;   // D = 256: per-CTA staging workspace (pair_ws_bytes), else unused
+  // Offsets delta and -delta carry swap images of each other; the pass runs over Pc items, item
+  // i updating pair index pidx[i] (delta - 1) and writing the image into pmir[i] (-1: -delta =
+  // delta).  pidx == nullptr: Pc = P items, item i = pair index i, no images.
+  int Pc;
+  const int* pidx;
+  const int* pmir;
 };
 
 struct DevStatus {
@@ -66,6 +72,9 @@ struct SmallArgs {
   const double* a2r;
   const double* part;
   double* part2;  // P: ||A1 rho - rho0||^2 + ||A2 rho - rho0||^2
+  // P: for the canonical member of {delta, -delta} the pair index of the other, -1 when
+  // -delta = delta, -2 for the member whose Lambda1, Lambda2 its partner writes; or nullptr
+  const int* ptie;
   DevStatus* st;
   double* rho0_partial;  // 128 * m*m chunk sums of the rho_0 reduction
 };

@@ -6,6 +6,12 @@
 //              the PSD projection (Eq. (rhoijTildeUpdate)), the Lambda update, the X' = X - eps G
 //              step for the block (Algorithm 6), the partial traces A1 rho, A2 rho and the
 //              per-delta terms of Eq. (feasErr) and of the energy.
+//              The offsets delta and -delta describe the same pairs of clusters seen from
+//              either end, and the update commutes with exchanging the two clusters (S): from a
+//              state with rho~_{-delta} = S rho~_delta S, Lambda likewise, Lambda1_{-delta} =
+//              Lambda2_delta and X_{0,-delta} = X_{0,delta}^T, the -delta results are the swap
+//              images of the delta ones.  So one group updates the canonical member of each
+//              pair {delta, -delta} and writes the images for the other: half the eigensolves.
 // k_rho0     : one CTA.  rho_0 update (Eq. (rhoiUpdate), translation-invariant form) with the
 //              trace shift, and X'_00 = X_00 - eps G_00[rho_0].
 // k_dual12   : Lambda1/Lambda2 updates (they need the new rho_0) and their feasibility terms.
@@ -45,7 +51,7 @@ struct PairSmem {
 
 // Arithmetic in T (double, or float in the mixed-precision sweep); the state stays float64.
 template <int D, typename T>
-__global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
+__global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupShape<D>::MINB)
     k_pair(const PairArgs a) {
   constexpr int m = PairShape<D>::m, NT = PairShape<D>::NT, LD = PairShape<D>::LD;
   constexpr int GPC = PairShape<D>::GPC;
@@ -70,7 +76,9 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
   const T c0 = T(1) / mu, c1 = T(1) / (mu + alpha), c2 = T(1) / (mu + T(2) * alpha);
   const T imu = T(1) / mu;
 
-  for (long p = (long)blockIdx.x * GPC + g; p < a.P; p += (long)gridDim.x * GPC) {
+  for (long it = (long)blockIdx.x * GPC + g; it < a.Pc; it += (long)gridDim.x * GPC) {
+    const long p = a.pidx ? a.pidx[it] : it;
+    const long pm = a.pidx ? a.pmir[it] : -1;  // pair index of -delta, or -1
     const long dl = p + 1;  // linear cluster offset delta
     const double* rt = a.rt + p * D * D;
     const double* lam = a.lam + p * D * D;
@@ -81,6 +89,13 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
     const double* Hb = hs >= 0 ? a.hb + (long)hs * D * D : nullptr;
 
     for (int e = tid; e < D * D; e += NT) Xs[e] = (T)Xb[e];
+    if (pm >= 0) {
+      // the multipliers of -delta as images of these, before the rho_0 reduction reads them
+      for (int idx = tid; idx < m * m; idx += NT) {
+        a.lam1[pm * m * m + idx] = l2[idx];
+        a.lam2[pm * m * m + idx] = l1[idx];
+      }
+    }
     gsync<NT>();
     // right-hand side of Eq. (rhoijUpdate) with H' of Eq. (effHam)
     for (int e = tid; e < D * D; e += NT) {
@@ -207,16 +222,28 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
     T rr = T(0), en = T(0);
     double* rtw = a.rt + p * D * D;
     double* lamw = a.lam + p * D * D;
+    // swap images for -delta: rho~ and Lambda conjugated by S, X' transposed
+    double* rtm = pm >= 0 ? a.rt + pm * D * D : nullptr;
+    double* lamm = pm >= 0 ? a.lam + pm * D * D : nullptr;
+    double* Xm = pm >= 0 ? a.X + (pm + 1) * D * D : nullptr;
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
       const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
       const T rho = R[e];
       const T rtn = A[i * LD + j];
       const T h = Hb ? (T)Hb[e] : T(0);
-      lamw[e] = (double)((T)lam[e] + mu * (rtn - rho));
-      rtw[e] = (double)rtn;
+      const double lamn = (double)((T)lam[e] + mu * (rtn - rho));
       // X'_{0,delta} = X_{0,delta} - eps G_{0,delta}[rho], G entry (a,b),(c,d) = rho_{(a,d),(b,c)}
-      Xb[e] = (double)(Xs[e] - eps * R[(pa * m + pd) * D + (pb * m + pc)]);
+      const double xn = (double)(Xs[e] - eps * R[(pa * m + pd) * D + (pb * m + pc)]);
+      lamw[e] = lamn;
+      rtw[e] = (double)rtn;
+      Xb[e] = xn;
+      if (pm >= 0) {
+        const int es = (pb * m + pa) * D + (pd * m + pc);
+        lamm[es] = lamn;
+        rtm[es] = (double)rtn;
+        Xm[j * D + i] = xn;
+      }
       rr += (rho - rtn) * (rho - rtn);
       en += h * R[j * D + i];
     }
@@ -229,12 +256,20 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC)
       }
       a.a1r[p * m * m + idx] = (double)s1;
       a.a2r[p * m * m + idx] = (double)s2;
+      if (pm >= 0) {
+        a.a1r[pm * m * m + idx] = (double)s2;
+        a.a2r[pm * m * m + idx] = (double)s1;
+      }
     }
     rr = gsum<NT>(rr, red);
     en = gsum<NT>(en, red);
     if (tid == 0) {
       a.part[p * 2 + 0] = (double)rr;
       a.part[p * 2 + 1] = (double)en;
+      if (pm >= 0) {
+        a.part[pm * 2 + 0] = (double)rr;
+        a.part[pm * 2 + 1] = (double)en;
+      }
     }
     gsync<NT>();
   }
@@ -251,7 +286,7 @@ cudaError_t launch_pair_t(const PairArgs& a, cudaStream_t s) {
     e = smem_once(k_pair<D, T>, smem, mask);
     if (e != cudaSuccess) return e;
   }
-  long blocks = (a.P + GPC - 1) / GPC;
+  long blocks = (a.Pc + GPC - 1) / GPC;
   const long res = G ? (long)big_grid() : resident_grid((const void*)k_pair<D, T>, NT * GPC, smem);
   if (blocks > res) blocks = res;
   if (blocks < 1) blocks = 1;
@@ -327,23 +362,37 @@ __global__ void __launch_bounds__(256) k_rho0(const SmallArgs a, const double* p
 }
 
 // ---------------------------------------------------------------- Lambda1, Lambda2
+// One warp per pair offset.  With ties (see k_pair) the canonical member of {delta, -delta}
+// also writes the other's multipliers, Lambda1_{-delta} = Lambda2_delta and Lambda2_{-delta} =
+// Lambda1_delta, so the two stay exact swap images.
 __global__ void k_dual12(const SmallArgs a) {
   const int lane = threadIdx.x & 31;
   const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int mm = a.m * a.m;
   if (w >= a.P) return;
+  const long tie = a.ptie ? a.ptie[w] : -1;
+  if (tie == -2) return;  // uniform over the warp
   double s = 0.0;
   for (int idx = lane; idx < mm; idx += 32) {
     const double r0 = a.rho0[idx];
     const double d1 = a.a1r[w * mm + idx] - r0;
     const double d2 = a.a2r[w * mm + idx] - r0;
-    a.lam1[w * mm + idx] += a.nu * d1;
-    a.lam2[w * mm + idx] += a.nu * d2;
+    const double n1 = a.lam1[w * mm + idx] + a.nu * d1;
+    const double n2 = a.lam2[w * mm + idx] + a.nu * d2;
+    a.lam1[w * mm + idx] = n1;
+    a.lam2[w * mm + idx] = n2;
+    if (tie >= 0) {
+      a.lam1[tie * mm + idx] = n2;
+      a.lam2[tie * mm + idx] = n1;
+    }
     s += d1 * d1 + d2 * d2;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) a.part2[w] = s;
+  if (lane == 0) {
+    a.part2[w] = s;
+    if (tie >= 0) a.part2[tie] = s;
+  }
 }
 
 // ---------------------------------------------------------------- status (one CTA)

@@ -238,6 +238,87 @@ def test_full_size_workload_matches_oracle(ve, prec):
         ve.ve_destroy(h)
 
 
+def _swap_image(B, m):
+    """P B P for D x D blocks (last two axes), P exchanging the two clusters' factors."""
+    sw = np.array([b * m + a for a in range(m) for b in range(m)])
+    return B[..., sw, :][..., :, sw]
+
+
+@pytest.mark.parametrize("lattice,cluster,kind,x", [((12,), (2,), "tfim", 0.8),
+                                                   ((4, 6), (2, 1), "xxz", 0.5),
+                                                   ((8,), (4,), "tfim", 1.0)])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_tied_offsets_are_swap_images(ve, lattice, cluster, kind, x, prec):
+    """After sweeps from the initial state the -delta blocks are the swap images of the delta
+    blocks: rho~ and Lambda conjugated by the factor exchange and Lambda1, Lambda2 exchanged,
+    bit for bit; X_{0,-delta} = X_{0,delta}^T to the rounding of the DFT."""
+    dim = len(lattice)
+    pb = vo.Problem(mo.cluster_model(lattice, cluster, *_terms(kind, dim, x)))
+    h = ve.ve_create(lattice, cluster, _ham(ve, kind, dim, x), ve.ve_default_options(precision=prec))
+    try:
+        ve.ve_iterate(h, 7, 0.0)
+        st = vo.unpack_state(pb, ve.ve_get_state(h))
+    finally:
+        ve.ve_destroy(h)
+    neg = vo.neg_index(pb.M)
+    tied = neg[1:] != np.arange(1, pb.N)  # offsets with -delta != delta; the others are
+    img = neg[1:][tied] - 1               # updated on their own, symmetric to rounding
+    for key in ('rt', 'lam'):
+        np.testing.assert_array_equal(st[key][img], _swap_image(st[key], pb.m)[tied])
+        assert relerr(st[key][~tied], _swap_image(st[key], pb.m)[~tied]) < (
+            10 * RTOL32 if prec == 1 else state_tol(prec))
+    np.testing.assert_array_equal(st['lam1'][img], st['lam2'][tied])
+    np.testing.assert_array_equal(st['lam2'][img], st['lam1'][tied])
+    xerr = relerr(st['X'][neg], np.swapaxes(st['X'], 1, 2))
+    assert xerr < (10 * RTOL32 if prec == 1 else state_tol(prec)), xerr
+
+
+def test_first_sweep_takes_the_canonical_members(ve):
+    """A state set without the swap symmetry between delta and -delta: a sweep reads, of each
+    pair {delta, -delta}, the member with the smaller linear index, so it matches the oracle's
+    sweep from the state whose other members are replaced by the images of those."""
+    lattice, cluster = (12,), (2,)
+    pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 0.8, 1)))
+    st = vo.initial_state(pb)
+    for _ in range(4):
+        vo.iterate(pb, st)
+    g = np.random.default_rng(7)
+    symn = lambda *shape: (lambda Z: 0.5 * (Z + np.swapaxes(Z, -1, -2)))(g.normal(size=shape))
+    P, D, m = pb.N - 1, pb.D, pb.m
+    st['rt'] = st['rt'] + 1e-3 * symn(P, D, D)
+    st['lam'] = st['lam'] + 1e-3 * symn(P, D, D)
+    st['lam1'] = st['lam1'] + 1e-3 * symn(P, m, m)
+    st['lam2'] = st['lam2'] + 1e-3 * symn(P, m, m)
+    st['X'] = st['X'] + 1e-3 * g.normal(size=st['X'].shape)
+    neg = vo.neg_index(pb.M)
+    for dl in range(pb.N):
+        if neg[dl] == dl:  # offsets with -delta = delta (and X_00) keep the swap symmetry
+            st['X'][dl] = 0.5 * (st['X'][dl] + st['X'][dl].T)
+            if dl > 0:
+                for key in ('rt', 'lam'):
+                    st[key][dl - 1] = 0.5 * (st[key][dl - 1] + _swap_image(st[key][dl - 1], m))
+                l12 = 0.5 * (st['lam1'][dl - 1] + st['lam2'][dl - 1])
+                st['lam1'][dl - 1], st['lam2'][dl - 1] = l12, l12.copy()
+    given = vo.pack_state(pb, st)
+    for dl in range(1, pb.N):
+        nd = neg[dl]
+        if nd < dl:
+            st['rt'][dl - 1] = _swap_image(st['rt'][nd - 1], m)
+            st['lam'][dl - 1] = _swap_image(st['lam'][nd - 1], m)
+            st['lam1'][dl - 1] = st['lam2'][nd - 1]
+            st['lam2'][dl - 1] = st['lam1'][nd - 1]
+            st['X'][dl] = st['X'][nd].T
+    assert relerr(given, vo.pack_state(pb, st)) > 1e-4  # the given state lacks the symmetry
+    h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 0.8))
+    try:
+        ve.ve_set_state(h, given)
+        ve.ve_iterate(h, 1, 0.0)
+        vo.iterate(pb, st)
+        assert relerr(ve.ve_get_state(h), vo.pack_state(pb, st)) < RTOL64
+    finally:
+        ve.ve_destroy(h)
+
+
 def test_state_roundtrip_resume_and_determinism(ve):
     """Two handles with the same history agree bitwise.  A resume through get/set state
     restarts the eigensolves cold (the stored eigenvectors are not part of the state), so it

@@ -297,17 +297,24 @@ def test_algorithm6_equals_algorithm5(lattice, cluster, kind):
         np.testing.assert_allclose(st6[key], v5[key], atol=1e-10, err_msg=key)
 
 
-def test_swap_symmetry_is_preserved():
-    """rho~_{-d} = P rho~_d P, Lambda1_{-d} = Lambda2_d, X_{-d} = X_d^T (P swaps the clusters)."""
-    on, bonds = mo.tfim_terms(1.0, 1.1, 2)
-    pb = vo.Problem(mo.cluster_model((4, 6), (2, 1), on, bonds))
+@pytest.mark.parametrize("lattice,cluster,kind", [((4, 6), (2, 1), "tfim"), ((10,), (2,), "xxz"),
+                                                  ((9,), (3,), "tfim")])
+def test_swap_symmetry_is_preserved(lattice, cluster, kind):
+    """The offsets d and -d see the same pairs of clusters from either end: H_{-d} = P H_d P,
+    and from the initial state the iteration keeps rho~_{-d} = P rho~_d P, Lambda_{-d} =
+    P Lambda_d P, Lambda1_{-d} = Lambda2_d, X_{-d} = X_d^T (P swaps the clusters)."""
+    dim = len(lattice)
+    on, bonds = mo.tfim_terms(1.0, 1.1, dim) if kind == "tfim" else mo.xxz_terms(1.0, 0.6, dim)
+    pb = vo.Problem(mo.cluster_model(lattice, cluster, on, bonds))
     st = vo.initial_state(pb)
     for _ in range(60):
         vo.iterate(pb, st)
     m, D = pb.m, pb.D
     neg = vo.neg_index(pb.M)
     swap = np.eye(D)[[b * m + a for a in range(m) for b in range(m)]]
+    np.testing.assert_array_equal(pb.Hpair[neg[1:] - 1], swap @ pb.Hpair @ swap)
     np.testing.assert_allclose(st['rt'][neg[1:] - 1], swap @ st['rt'] @ swap, atol=1e-12)
+    np.testing.assert_allclose(st['lam'][neg[1:] - 1], swap @ st['lam'] @ swap, atol=1e-11)
     np.testing.assert_allclose(st['lam1'][neg[1:] - 1], st['lam2'], atol=1e-12)
     np.testing.assert_allclose(st['X'][neg], np.swapaxes(st['X'], 1, 2), atol=1e-12)
 
