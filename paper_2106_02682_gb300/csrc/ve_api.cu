@@ -625,7 +625,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
     return VE_ECUDA;
   }
   *h->hst = ds;
-  const int launches[VE_NSTAGE] = {1, 2, 1, 1, h->plan.npass, 1, h->plan.npass};
+  const int launches[VE_NSTAGE] = {1, 1, 1, 1, h->plan.npass, 1, h->plan.npass};
   for (int i = 0; i < VE_NSTAGE; ++i) h->stage_launches[i] = launches[i];
   *out = h;
   return VE_OK;

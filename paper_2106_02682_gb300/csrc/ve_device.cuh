@@ -34,7 +34,8 @@ __device__ __forceinline__ void gsync() {
 }
 
 // Sum over the group, identical result (same order) in every thread.  `red` is shared scratch
-// of NT/32 entries, used only when NT > 32.
+// of NT/32 entries, used only when NT > 32.  The warp sums are combined by warp 0 alone and
+// broadcast: float64 issue is scarce, so no other warp repeats that work.
 template <int NT, typename T>
 __device__ __forceinline__ T gsum(T v, T* red) {
 #pragma unroll
@@ -46,9 +47,15 @@ __device__ __forceinline__ T gsum(T v, T* red) {
     __syncthreads();
     if (lane == 0) red[w] = v;
     __syncthreads();
-    T s = T(0);
+    if (w == 0) {
+      T s = lane < NT / 32 ? red[lane] : T(0);
 #pragma unroll
-    for (int i = 0; i < NT / 32; ++i) s += red[i];
+      for (int o = 16; o > 0; o >>= 1) s += shfl_xor(s, o);
+      __syncwarp();
+      if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    const T s = red[0];
     __syncthreads();
     return s;
   }
@@ -65,9 +72,15 @@ __device__ __forceinline__ T gmin(T v, T* red) {
     __syncthreads();
     if (lane == 0) red[w] = v;
     __syncthreads();
-    T s = red[0];
+    if (w == 0) {
+      T s = red[lane < NT / 32 ? lane : 0];
 #pragma unroll
-    for (int i = 1; i < NT / 32; ++i) s = fmin(s, red[i]);
+      for (int o = 16; o > 0; o >>= 1) s = fmin(s, shfl_xor(s, o));
+      __syncwarp();
+      if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    const T s = red[0];
     __syncthreads();
     return s;
   }
@@ -85,6 +98,18 @@ __device__ __forceinline__ void rr_pair(int n, int r, int k, int& p, int& q) {
   }
   p = a < b ? a : b;
   q = a < b ? b : a;
+}
+
+// Entry t of the upper triangle (i <= j) of an n x n matrix in row-major order, so a group
+// can share out the n (n + 1) / 2 entries of a symmetric result without idle lanes.  Row
+// r = n - 1 - i from the bottom holds entries r (r + 1) / 2 ... of the reversed count u.
+__device__ __forceinline__ void tri_index(int n, int t, int& i, int& j) {
+  const int u = n * (n + 1) / 2 - 1 - t;
+  int r = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+  if ((r + 1) * (r + 2) / 2 <= u) ++r;
+  if (r * (r + 1) / 2 > u) --r;
+  i = n - 1 - r;
+  j = n - 1 - (u - r * (r + 1) / 2);
 }
 
 template <typename T>

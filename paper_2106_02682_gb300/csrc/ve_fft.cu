@@ -303,21 +303,20 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
         Wi[i * LD + jj] = xi;
       }
       gsync<NT>();
-      for (int e = tid; e < D * D; e += NT) {  // A = V^H W, Hermitian
-        const int i = e / D, jj = e % D;
-        if (i <= jj) {
-          T xr = T(0), xi = T(0);
-          for (int k = 0; k < D; ++k) {
-            const T ar = Vr[k * LD + i], ai = -Vi[k * LD + i];
-            const T br = Wr[k * LD + jj], bi = Wi[k * LD + jj];
-            xr += ar * br - ai * bi;
-            xi += ar * bi + ai * br;
-          }
-          Ar[i * LD + jj] = xr;
-          Ar[jj * LD + i] = xr;
-          Ai[i * LD + jj] = (i == jj) ? T(0) : xi;
-          Ai[jj * LD + i] = (i == jj) ? T(0) : -xi;
+      for (int t = tid; t < D * (D + 1) / 2; t += NT) {  // A = V^H W, Hermitian
+        int i, jj;
+        tri_index(D, t, i, jj);
+        T xr = T(0), xi = T(0);
+        for (int k = 0; k < D; ++k) {
+          const T ar = Vr[k * LD + i], ai = -Vi[k * LD + i];
+          const T br = Wr[k * LD + jj], bi = Wi[k * LD + jj];
+          xr += ar * br - ai * bi;
+          xi += ar * bi + ai * br;
         }
+        Ar[i * LD + jj] = xr;
+        Ar[jj * LD + i] = xr;
+        Ai[i * LD + jj] = (i == jj) ? T(0) : xi;
+        Ai[jj * LD + i] = (i == jj) ? T(0) : -xi;
       }
       gsync<NT>();
       nsw = jacobi_herm<T, D, LD, NT, true, false>(Ar, Ai, Vr, Vi, cs, red, tid);
@@ -340,22 +339,21 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
     }
     gsync<NT>();
     // Y = V diag(max(w,0)) V^H, written back into (Ar, Ai)
-    for (int f = tid; f < D * D; f += NT) {
-      const int i = f / D, jj = f % D;
-      if (i <= jj) {
-        T yr = T(0), yi = T(0);
-        for (int k = 0; k < D; ++k) {
-          const T w = W[k];
-          const T air = Vr[i * LD + k], aii = Vi[i * LD + k];
-          const T ajr = Vr[jj * LD + k], aji = Vi[jj * LD + k];
-          yr += w * (air * ajr + aii * aji);
-          yi += w * (aii * ajr - air * aji);
-        }
-        Ar[i * LD + jj] = yr;
-        Ai[i * LD + jj] = yi;
-        Ar[jj * LD + i] = yr;
-        Ai[jj * LD + i] = -yi;
+    for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+      int i, jj;
+      tri_index(D, t, i, jj);
+      T yr = T(0), yi = T(0);
+      for (int k = 0; k < D; ++k) {
+        const T w = W[k];
+        const T air = Vr[i * LD + k], aii = Vi[i * LD + k];
+        const T ajr = Vr[jj * LD + k], aji = Vi[jj * LD + k];
+        yr += w * (air * ajr + aii * aji);
+        yi += w * (aii * ajr - air * aji);
       }
+      Ar[i * LD + jj] = yr;
+      Ai[i * LD + jj] = yi;
+      Ar[jj * LD + i] = yr;
+      Ai[jj * LD + i] = -yi;
     }
     gsync<NT>();
     // pack Y_k (and Y_{-k} = conj Y_k) back, scaled by 1/N

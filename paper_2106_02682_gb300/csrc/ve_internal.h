@@ -57,7 +57,8 @@ struct DevStatus {
   double energy, feas, d_energy, residual;
   double e_prev;
   double h0rho0;  // Tr[H_0 rho_0] of the current sweep
-  double pad;
+  unsigned int done;  // CTAs of the running multi-CTA reduction finished (0 between kernels)
+  unsigned int pad;
 };
 
 struct SmallArgs {
@@ -76,7 +77,7 @@ struct SmallArgs {
   // -delta = delta, -2 for the member whose Lambda1, Lambda2 its partner writes; or nullptr
   const int* ptie;
   DevStatus* st;
-  double* rho0_partial;  // 128 * m*m chunk sums of the rho_0 reduction
+  double* rho0_partial;  // 128 * m*m chunk sums of the rho_0 reduction, then the status sums
 };
 
 // Number of CTAs that keep every SM busy for a kernel with the given block shape.

@@ -12,10 +12,12 @@
 //              Lambda2_delta and X_{0,-delta} = X_{0,delta}^T, the -delta results are the swap
 //              images of the delta ones.  So one group updates the canonical member of each
 //              pair {delta, -delta} and writes the images for the other: half the eigensolves.
-// k_rho0     : one CTA.  rho_0 update (Eq. (rhoiUpdate), translation-invariant form) with the
-//              trace shift, and X'_00 = X_00 - eps G_00[rho_0].
+// k_rho0     : rho_0 update (Eq. (rhoiUpdate), translation-invariant form) with the trace
+//              shift, and X'_00 = X_00 - eps G_00[rho_0]: every CTA sums a chunk of offsets, the
+//              last CTA to finish adds the chunk sums and updates rho_0.
 // k_dual12   : Lambda1/Lambda2 updates (they need the new rho_0) and their feasibility terms.
-// k_status   : one CTA.  Energy per spin, Eq. (feasErr), |energy change|, residual.
+// k_status   : energy per spin, Eq. (feasErr), |energy change|, residual (CTA sums, then
+//              the last CTA).
 // All reductions run in a fixed order, so a sweep is bitwise reproducible.
 #include "ve_device.cuh"
 #include "ve_internal.h"
@@ -162,14 +164,13 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
       }
     }
     // C = rho - Lambda / mu, symmetrised, into A
-    for (int e = tid; e < D * D; e += NT) {
-      const int i = e / D, j = e % D;
-      if (i <= j) {
-        const T v = T(0.5) * (R[i * D + j] + R[j * D + i]) -
-                    T(0.5) * ((T)lam[i * D + j] + (T)lam[j * D + i]) * imu;
-        A[i * LD + j] = v;
-        A[j * LD + i] = v;
-      }
+    for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+      int i, j;
+      tri_index(D, t, i, j);
+      const T v = T(0.5) * (R[i * D + j] + R[j * D + i]) -
+                  T(0.5) * ((T)lam[i * D + j] + (T)lam[j * D + i]) * imu;
+      A[i * LD + j] = v;
+      A[j * LD + i] = v;
     }
     gsync<NT>();
     if (a.warm) {
@@ -182,15 +183,14 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
         Wt[i * LD + j] = acc;
       }
       gsync<NT>();
-      for (int e = tid; e < D * D; e += NT) {
-        const int i = e / D, j = e % D;
-        if (i <= j) {
-          T acc = T(0);
+      for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+        int i, j;
+        tri_index(D, t, i, j);
+        T acc = T(0);
 #pragma unroll 4
-          for (int k = 0; k < D; ++k) acc += V[k * LD + i] * Wt[k * LD + j];
-          A[i * LD + j] = acc;
-          A[j * LD + i] = acc;
-        }
+        for (int k = 0; k < D; ++k) acc += V[k * LD + i] * Wt[k * LD + j];
+        A[i * LD + j] = acc;
+        A[j * LD + i] = acc;
       }
       gsync<NT>();
       nsw = jacobi_sym<T, D, LD, NT, true, false>(A, V, cs, red, tid);
@@ -208,15 +208,14 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
     }
     gsync<NT>();
     // rho~ = V diag(max(w, 0)) V^T
-    for (int e = tid; e < D * D; e += NT) {
-      const int i = e / D, j = e % D;
-      if (i <= j) {
-        T s = T(0);
+    for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+      int i, j;
+      tri_index(D, t, i, j);
+      T s = T(0);
 #pragma unroll 4
-        for (int k = 0; k < D; ++k) s += W[k] * V[i * LD + k] * V[j * LD + k];
-        A[i * LD + j] = s;
-        A[j * LD + i] = s;
-      }
+      for (int k = 0; k < D; ++k) s += W[k] * V[i * LD + k] * V[j * LD + k];
+      A[i * LD + j] = s;
+      A[j * LD + i] = s;
     }
     gsync<NT>();
     T rr = T(0), en = T(0);
@@ -295,12 +294,12 @@ cudaError_t launch_pair_t(const PairArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- rho_0 and X'_00
-// Stage 1: RHO0_CHUNKS CTAs each sum a contiguous range of offsets delta of
-// nu A1[rho_{0,delta}] + Lambda1_{0,delta} (m*m entries); stage 2 (one CTA) adds the chunk sums
-// in order.  Both orders are fixed, so the result is reproducible bit for bit.
+// RHO0_CHUNKS CTAs each sum a contiguous range of offsets delta of nu A1[rho_{0,delta}] +
+// Lambda1_{0,delta} (m*m entries); the last CTA to finish (a counter in the status block) adds
+// the chunk sums in order.  Both orders are fixed, so the result is reproducible bit for bit.
 constexpr int RHO0_CHUNKS = 128;
 
-__global__ void __launch_bounds__(256) k_rho0_partial(const SmallArgs a, double* partial) {
+__global__ void __launch_bounds__(256) k_rho0(const SmallArgs a, double* partial) {
   const int mm = a.m * a.m;
   const long per = (a.P + RHO0_CHUNKS - 1) / RHO0_CHUNKS;
   const long lo = blockIdx.x * per, hi = min((long)a.P, lo + per);
@@ -320,16 +319,30 @@ __global__ void __launch_bounds__(256) k_rho0_partial(const SmallArgs a, double*
     for (int c = 0; c < subs; ++c) s += S[c * mm + t];
     partial[blockIdx.x * mm + t] = s;
   }
-}
-
-__global__ void __launch_bounds__(256) k_rho0(const SmallArgs a, const double* partial) {
+  __threadfence();
+  __shared__ bool last;
+  __syncthreads();
+  if (t == 0) last = atomicAdd(&a.st->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // the last CTA: rho_0 from the chunk sums (read past L1: other CTAs wrote them), each entry
+  // summed by subs threads over interleaved chunks, then in order over the threads
+  {
+    double acc2 = 0.0;
+    if (t < subs * mm) {
+      const int idx = t % mm, c0 = t / mm;
+      for (int c = c0; c < RHO0_CHUNKS; c += subs) acc2 += __ldcg(partial + c * mm + idx);
+    }
+    S[t] = acc2;
+  }
+  __syncthreads();
   __shared__ double rp[256];
   __shared__ double red[8];
-  const int m = a.m, mm = m * m, D = a.D;
-  const int t = threadIdx.x;
+  const int m = a.m, D = a.D;
   if (t < mm) {
     double s = 0.0;
-    for (int c = 0; c < RHO0_CHUNKS; ++c) s += partial[c * mm + t];
+    for (int c = 0; c < subs; ++c) s += S[c * mm + t];
     // H'_0 = H_0 - sum_a X_{(a,b),(a,d)}  (Eq. (effHam) with matrix units)
     const int b = t / m, d = t % m;
     double hx = 0.0;
@@ -358,7 +371,10 @@ __global__ void __launch_bounds__(256) k_rho0(const SmallArgs a, const double* p
   double h = 0.0;
   if (t < mm) h = a.H0[t] * rp[(t % m) * m + (t / m)];
   h = gsum<256>(h, red);
-  if (t == 0) a.st->h0rho0 = h;
+  if (t == 0) {
+    a.st->h0rho0 = h;
+    a.st->done = 0u;  // ready for the next sweep
+  }
 }
 
 // ---------------------------------------------------------------- Lambda1, Lambda2
@@ -395,11 +411,17 @@ __global__ void k_dual12(const SmallArgs a) {
   }
 }
 
-// ---------------------------------------------------------------- status (one CTA)
-__global__ void __launch_bounds__(256) k_status(const SmallArgs a) {
+// ---------------------------------------------------------------- status
+// STATUS_CTAS CTAs each sum a contiguous range of offsets (float64 adds are spread over as many
+// SMs); the last CTA to finish adds the CTA sums in order and writes the status block.
+constexpr int STATUS_CTAS = 32;
+
+__global__ void __launch_bounds__(256) k_status(const SmallArgs a, double* partial) {
   __shared__ double red[8];
+  const long per = (a.P + STATUS_CTAS - 1) / STATUS_CTAS;
+  const long lo = blockIdx.x * per, hi = min((long)a.P, lo + per);
   double rr = 0.0, en = 0.0, ff = 0.0;
-  for (long p = threadIdx.x; p < a.P; p += 256) {
+  for (long p = lo + threadIdx.x; p < hi; p += 256) {
     rr += a.part[p * 2 + 0];
     en += a.part[p * 2 + 1];
     ff += a.part2[p];
@@ -408,7 +430,27 @@ __global__ void __launch_bounds__(256) k_status(const SmallArgs a) {
   en = gsum<256>(en, red);
   ff = gsum<256>(ff, red);
   if (threadIdx.x == 0) {
+    partial[blockIdx.x * 3 + 0] = rr;
+    partial[blockIdx.x * 3 + 1] = en;
+    partial[blockIdx.x * 3 + 2] = ff;
+  }
+  __threadfence();
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&a.st->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int t = threadIdx.x;
+  rr = t < STATUS_CTAS ? __ldcg(partial + t * 3 + 0) : 0.0;
+  en = t < STATUS_CTAS ? __ldcg(partial + t * 3 + 1) : 0.0;
+  ff = t < STATUS_CTAS ? __ldcg(partial + t * 3 + 2) : 0.0;
+  rr = gsum<256>(rr, red);
+  en = gsum<256>(en, red);
+  ff = gsum<256>(ff, red);
+  if (t == 0) {
     DevStatus* st = a.st;
+    st->done = 0u;
     const double E = (st->h0rho0 + 0.5 * en) / a.L;
     const double feas = sqrt((rr + ff) / a.P);
     const double dE = isfinite(st->e_prev) ? fabs(E - st->e_prev) : INFINITY;
@@ -468,10 +510,7 @@ int big_grid() {
 }
 
 cudaError_t launch_rho0(const SmallArgs& a, cudaStream_t s) {
-  k_rho0_partial<<<RHO0_CHUNKS, 256, 0, s>>>(a, a.rho0_partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_rho0<<<1, 256, 0, s>>>(a, a.rho0_partial);
+  k_rho0<<<RHO0_CHUNKS, 256, 0, s>>>(a, a.rho0_partial);
   return cudaGetLastError();
 }
 
@@ -483,7 +522,7 @@ cudaError_t launch_dual12(const SmallArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_status(const SmallArgs& a, cudaStream_t s) {
-  k_status<<<1, 256, 0, s>>>(a);
+  k_status<<<STATUS_CTAS, 256, 0, s>>>(a, a.rho0_partial);
   return cudaGetLastError();
 }
 
