@@ -128,7 +128,9 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
 /* Run sweeps of Algorithm 6 until max_iter sweeps or, when tol > 0, until the residual is
  * <= tol at a read-back (every check_every sweeps).  In VE_PREC_MIXED the sweeps use float32
  * projections until the residual reaches tol (or stops falling: no 1 % gain over 100
- * read-backs), then continue in VE_PREC_DF64 arithmetic until the residual is <= tol again.
+ * read-backs, counted across calls), then continue in VE_PREC_DF64 arithmetic until the
+ * residual is <= tol again; with tol <= 0 they stay in float32.  ve_set_state returns a handle
+ * to the float32 phase.
  * Writes the last status to *out (may be NULL).  Returns VE_OK if converged (or tol <= 0 and
  * max_iter sweeps ran), VE_NOT_CONVERGED, VE_ENONFINITE, VE_EINVAL, VE_ECUDA.  Synchronous. */
 int ve_iterate(ve_handle* h, long max_iter, double tol, ve_status* out);

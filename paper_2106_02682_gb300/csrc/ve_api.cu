@@ -185,6 +185,8 @@ struct ve_handle {
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
   bool fp64_phase = false;  // MIXED: switched to the float64-accurate phase
+  double mx_best = INFINITY;  // MIXED float32 phase: best residual and read-backs without a
+  int mx_stall = 0;           // 1 % gain, kept across ve_iterate calls
   // per-stage profiling
   bool prof = false;
   cudaEvent_t ev[VE_NSTAGE + 1] = {};
@@ -678,6 +680,8 @@ int ve_set_state(ve_handle* h, const double* host, size_t bytes) {
   VE_CU(cudaMemcpyAsync(h->dst, h->hst, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
   VE_CU(cudaStreamSynchronize(h->stream));
   h->fp64_phase = false;
+  h->mx_best = INFINITY;
+  h->mx_stall = 0;
   h->vvalid[0] = h->vvalid[1] = h->vvalid[2] = false;
   return VE_OK;
 }
@@ -738,8 +742,6 @@ int handle_arith(const ve_handle* h) {
 // until the residual meets tol or has not fallen by 1 % over 100 read-backs (the float32
 // rounding floor), then float64 sweeps until the residual meets tol.
 struct IterCtl {
-  double best = INFINITY;
-  int stall = 0;
   bool finished = false;
   int rc = VE_NOT_CONVERGED;
 };
@@ -753,13 +755,13 @@ void ctl_update(ve_handle* h, IterCtl& c, const ve_status& s, double tol) {
   if (tol <= 0) return;
   const bool fp32 = h->opt.precision == VE_PREC_MIXED && !h->fp64_phase;
   if (fp32) {
-    if (s.residual < 0.99 * c.best) {
-      c.best = s.residual;
-      c.stall = 0;
+    if (s.residual < 0.99 * h->mx_best) {
+      h->mx_best = s.residual;
+      h->mx_stall = 0;
     } else {
-      ++c.stall;
+      ++h->mx_stall;
     }
-    if (s.residual <= tol || c.stall >= 100) h->fp64_phase = true;
+    if (s.residual <= tol || h->mx_stall >= 100) h->fp64_phase = true;
   } else if (s.residual <= tol) {
     c.finished = true;
     c.rc = VE_OK;

@@ -42,31 +42,67 @@ def test_gpu_network_matches_the_reference(ve, n_in, hidden, layers, n_out, n):
         ve.ve_mlp_destroy(m)
 
 
-def test_warm_start_beats_cold_start_on_held_out_fields(ve):
+LATTICE, CLUSTER = (40,), (2,)
+
+
+@pytest.fixture(scope="module")
+def fitted(ve):
     from paper_2106_02682_gb300.warmstart import WarmStart
-    lattice, cluster = (40,), (2,)
-    ws = WarmStart(lattice, cluster, "tfim", n_components=12)
-    try:
-        xs = np.linspace(0.5, 1.5, 11)
-        states, _ = ws.training_states(xs, tol=1e-8, max_iter=40000)
-        assert ws.fit(xs, states, train_steps=3000) < 1e-2
-        opt = ve.ve_default_options(precision=1)
-        cold_total = warm_total = 0
-        for h in (0.65, 0.95, 1.25):
-            hc = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, h), opt)
-            hw = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, h), opt)
-            try:
-                _, sc = ve.ve_iterate(hc, 40000, 1e-6)
-                ws.apply(hw, h)
-                assert ve.ve_bound(hw).x_min_eig > -1e-9          # X is PSD after the projection
-                _, sw = ve.ve_iterate(hw, 40000, 1e-6)
-                cold_total += sc.iter
-                warm_total += sw.iter
-                bound = ve.ve_bound(hw).bound_per_spin
-                assert bound <= mo.tfim_chain_jw_energy(40, 1.0, h) / 40     # still a lower bound
-            finally:
-                ve.ve_destroy(hc)
-                ve.ve_destroy(hw)
-        assert warm_total < 0.7 * cold_total, (warm_total, cold_total)
-    finally:
-        ws.close()
+    ws = WarmStart(LATTICE, CLUSTER, "tfim", n_components=12)
+    xs = np.linspace(0.5, 1.5, 11)
+    states, _ = ws.training_states(xs, tol=1e-8, max_iter=40000)
+    loss = ws.fit(xs, states, train_steps=3000)
+    yield ws, loss
+    ws.close()
+
+
+def test_warm_start_beats_cold_start_on_held_out_fields(ve, fitted):
+    ws, loss = fitted
+    lattice, cluster = LATTICE, CLUSTER
+    assert loss < 1e-2
+    opt = ve.ve_default_options(precision=1)
+    cold_total = warm_total = 0
+    for h in (0.65, 0.95, 1.25):
+        hc = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, h), opt)
+        hw = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, h), opt)
+        try:
+            _, sc = ve.ve_iterate(hc, 40000, 1e-6)
+            ws.apply(hw, h)
+            assert ve.ve_bound(hw).x_min_eig > -1e-9          # X is PSD after the projection
+            _, sw = ve.ve_iterate(hw, 40000, 1e-6)
+            cold_total += sc.iter
+            warm_total += sw.iter
+            bound = ve.ve_bound(hw).bound_per_spin
+            assert bound <= mo.tfim_chain_jw_energy(40, 1.0, h) / 40     # still a lower bound
+        finally:
+            ve.ve_destroy(hc)
+            ve.ve_destroy(hw)
+    assert warm_total < 0.7 * cold_total, (warm_total, cold_total)
+
+
+def test_race_certifies_every_target_no_later_than_the_cold_start(ve, fitted):
+    """Warm and cold copies raced in one batch: every instance reaches its target (the float64
+    bound at the residual 1e-6, less 1e-6), never later than a cold mixed solve checked on the
+    same 50-sweep grid, and every certified bound stays below the exact energy."""
+    from paper_2106_02682_gb300.warmstart import race_to_bound
+    ws, _ = fitted
+    fields = [0.65, 0.95, 1.25]
+    targets, cold = [], []
+    for h in fields:
+        hf = ve.ve_create(LATTICE, CLUSTER, ve.ve_ham_tfim(1, 1.0, h), ve.ve_default_options(precision=0))
+        hc = ve.ve_create(LATTICE, CLUSTER, ve.ve_ham_tfim(1, 1.0, h), ve.ve_default_options(precision=1))
+        try:
+            ve.ve_iterate(hf, 40000, 1e-6)
+            targets.append(ve.ve_bound(hf).bound_per_spin - 1e-6)
+            while True:
+                _, st = ve.ve_iterate(hc, 50, 1e-13)
+                if ve.ve_bound(hc).bound_per_spin >= targets[-1] or st.iter >= 40000:
+                    cold.append(st.iter)
+                    break
+        finally:
+            ve.ve_destroy(hf)
+            ve.ve_destroy(hc)
+    race = race_to_bound(LATTICE, CLUSTER, "tfim", fields, targets, ws, chunk=50, max_sweeps=40000)
+    for h, t, c, r in zip(fields, targets, cold, race):
+        assert r["sweeps"] is not None and r["sweeps"] <= c, (h, r, c)
+        assert t <= r["bound_per_spin"] <= mo.tfim_chain_jw_energy(40, 1.0, h) / 40
