@@ -148,7 +148,10 @@ int ve_dims(const ve_handle* h, int* N, int* m, int* D);
 /* Packed state: rho_0 (m^2), rho~ (P D^2), Lambda (P D^2), Lambda1 (P m^2), Lambda2 (P m^2),
  * X (N D^2), P = N - 1, float64, each block row-major.  ve_state_size gives the byte count;
  * get/set copy through `host` (host memory, bytes must equal that size; VE_EINVAL otherwise).
- * ve_set_state clears the stored previous energy, so the next d_energy is +inf.
+ * ve_set_state clears the stored previous energy, so the next d_energy is +inf.  The
+ * eigenvectors of the last projections are not part of the state; the handle keeps them as the
+ * starting point of the next sweep's eigensolves (any orthogonal start converges), so a state
+ * read and set back on the same handle continues bit for bit, and on a fresh handle to rounding.
  *
  * Opposite offsets delta and -delta describe the same pairs of clusters seen from either end,
  * and a sweep commutes with exchanging the two clusters of a pair.  A sweep therefore updates,

@@ -304,10 +304,10 @@ int accumulate_profile(ve_handle* h) {
   return VE_OK;
 }
 
-// Run `count` sweeps.  The first sweep of a precision after ve_create / ve_set_state runs
-// directly and cold (Jacobi from V = I; it also sets kernel attributes outside any capture);
-// the others replay a captured one-sweep graph that starts every Jacobi from the eigenvectors
-// stored by the previous sweep.
+// Run `count` sweeps.  The first sweep of a precision on a handle runs directly and cold
+// (Jacobi from V = I; it also sets kernel attributes outside any capture); the others replay a
+// captured one-sweep graph that starts every Jacobi from the eigenvectors stored by the
+// previous sweep of that precision (kept across ve_set_state).
 int read_status(ve_handle* h, ve_status* out);
 
 int run_sweeps(ve_handle* h, long count, int arith) {
@@ -682,7 +682,8 @@ int ve_set_state(ve_handle* h, const double* host, size_t bytes) {
   h->fp64_phase = false;
   h->mx_best = INFINITY;
   h->mx_stall = 0;
-  h->vvalid[0] = h->vvalid[1] = h->vvalid[2] = false;
+  // the stored eigenvectors stay: any orthogonal start is valid for the Jacobi eigensolves, and
+  // those of the last sweep are the right one when the state set is near the handle's own
   return VE_OK;
 }
 

@@ -114,23 +114,31 @@ __device__ __forceinline__ void tri_index(int n, int t, int& i, int& j) {
 
 template <typename T>
 struct JacobiTol;
+// A sweep loop stops when off(A)^2 <= (n u)^2 ||A||_F^2, u the unit roundoff of the arithmetic:
+// the projection's error is at most off(A), and n u ||A|| is the rounding level of the n-term
+// sums of the reconstruction V diag V^T itself.  A fixed threshold would sit below the rounding
+// floor of the off-diagonal (~sqrt(n) u ||A||) for large n.
 template <>
 struct JacobiTol<double> {
-  static constexpr double rel2 = 1e-30;  // stop when off(A)^2 <= rel2 ||A||_F^2
-  static constexpr double big = 1e150;   // |tau| above which t = 1/(2 tau)
+  static constexpr double u = 1.1102230246251565e-16;  // 2^-53
+  static constexpr double big = 1e150;                 // |tau| above which t = 1/(2 tau)
   static constexpr int max_sweeps = 24;
 };
 template <>
 struct JacobiTol<float> {
-  static constexpr float rel2 = 1e-13f;
+  static constexpr double u = 5.9604644775390625e-08;  // 2^-24
   static constexpr float big = 1e18f;
   static constexpr int max_sweeps = 14;
 };
 template <>
 struct JacobiTol<df64> {
-  static constexpr double rel2 = 1e-28;  // df64 rounding is ~2^-48
+  static constexpr double u = 3.552713678800501e-15;   // 2^-48
   static constexpr double big = 1e18;
   static constexpr int max_sweeps = 24;
+};
+template <typename T, int n>
+struct JacobiStop {
+  static constexpr double rel2 = (n * JacobiTol<T>::u) * (n * JacobiTol<T>::u);
 };
 
 // Rotation (c, s) that annihilates the (p,q) entry of [[app, apq], [apq, aqq]] with
@@ -315,6 +323,10 @@ template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
 __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
   static_assert(n == 2 || n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
+  // blocks (GB) and eigenvector rows (GV) a thread loads before it stores any: a matrix staged
+  // in global memory (n > 64) needs several loads in flight per thread; every block and row of a
+  // round is disjoint from the others, so the reordering changes no result
+  constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
     const T a = A[(e / n) * LD + (e % n)];
@@ -336,7 +348,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
       }
     }
     off = gsum<NT>(off, red);
-    if (off <= T(JacobiTol<T>::rel2) * nrm) break;
+    if (off <= T(JacobiStop<T, n>::rel2) * nrm) break;
     for (int r = 0; r < n - 1; ++r) {
       // the rotation of each pair, and the pair's own 2x2 block made diagonal
       for (int k = tid; k < H; k += NT) {
@@ -356,38 +368,66 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
       if constexpr (H >= 2) {
         // the blocks (k1, k2), k1 < k2 -- enumerated as the pairs of a circle ordering of the
         // H pair indices -- and their transposes (k2, k1)
-        for (int b = tid; b < H * (H - 1) / 2; b += NT) {
-          int k1, k2;
-          rr_pair(H, b / (H / 2), b % (H / 2), k1, k2);
-          int p1, q1, p2, q2;
-          rr_pair(n, r, k1, p1, q1);
-          rr_pair(n, r, k2, p2, q2);
-          const T c1 = cs[k1], s1 = cs[H + k1], c2 = cs[k2], s2 = cs[H + k2];
-          const T m11 = A[p1 * LD + p2], m12 = A[p1 * LD + q2];
-          const T m21 = A[q1 * LD + p2], m22 = A[q1 * LD + q2];
-          const T x11 = c2 * m11 - s2 * m12, x12 = s2 * m11 + c2 * m12;
-          const T x21 = c2 * m21 - s2 * m22, x22 = s2 * m21 + c2 * m22;
-          const T y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
-          const T y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
-          A[p1 * LD + p2] = y11;
-          A[p2 * LD + p1] = y11;
-          A[p1 * LD + q2] = y12;
-          A[q2 * LD + p1] = y12;
-          A[q1 * LD + p2] = y21;
-          A[p2 * LD + q1] = y21;
-          A[q1 * LD + q2] = y22;
-          A[q2 * LD + q1] = y22;
+        constexpr int NB = H * (H - 1) / 2;
+        for (int b0 = tid; b0 < NB; b0 += GB * NT) {
+          int k1[GB], k2[GB], p1[GB], q1[GB], p2[GB], q2[GB];
+          T m11[GB], m12[GB], m21[GB], m22[GB];
+#pragma unroll
+          for (int g = 0; g < GB; ++g) {
+            const int b = b0 + g * NT;
+            if (b < NB) {
+              rr_pair(H, b / (H / 2), b % (H / 2), k1[g], k2[g]);
+              rr_pair(n, r, k1[g], p1[g], q1[g]);
+              rr_pair(n, r, k2[g], p2[g], q2[g]);
+              m11[g] = A[p1[g] * LD + p2[g]];
+              m12[g] = A[p1[g] * LD + q2[g]];
+              m21[g] = A[q1[g] * LD + p2[g]];
+              m22[g] = A[q1[g] * LD + q2[g]];
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < GB; ++g) {
+            if (b0 + g * NT < NB) {
+              const T c1 = cs[k1[g]], s1 = cs[H + k1[g]], c2 = cs[k2[g]], s2 = cs[H + k2[g]];
+              const T x11 = c2 * m11[g] - s2 * m12[g], x12 = s2 * m11[g] + c2 * m12[g];
+              const T x21 = c2 * m21[g] - s2 * m22[g], x22 = s2 * m21[g] + c2 * m22[g];
+              const T y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+              const T y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+              A[p1[g] * LD + p2[g]] = y11;
+              A[p2[g] * LD + p1[g]] = y11;
+              A[p1[g] * LD + q2[g]] = y12;
+              A[q2[g] * LD + p1[g]] = y12;
+              A[q1[g] * LD + p2[g]] = y21;
+              A[p2[g] * LD + q1[g]] = y21;
+              A[q1[g] * LD + q2[g]] = y22;
+              A[q2[g] * LD + q1[g]] = y22;
+            }
+          }
         }
       }
       if constexpr (VEC) {
-        for (int t = tid; t < n * H; t += NT) {
-          const int i = t / H, k = t % H;
-          int p, q;
-          rr_pair(n, r, k, p, q);
-          const T c = cs[k], s = cs[H + k];
-          const T vp = V[i * LD + p], vq = V[i * LD + q];
-          V[i * LD + p] = c * vp - s * vq;
-          V[i * LD + q] = s * vp + c * vq;
+        for (int t0 = tid; t0 < n * H; t0 += GV * NT) {
+          int ix[GV], kk[GV], pp[GV], qq[GV];
+          T vp[GV], vq[GV];
+#pragma unroll
+          for (int g = 0; g < GV; ++g) {
+            const int t = t0 + g * NT;
+            if (t < n * H) {
+              ix[g] = t / H;
+              kk[g] = t % H;
+              rr_pair(n, r, kk[g], pp[g], qq[g]);
+              vp[g] = V[ix[g] * LD + pp[g]];
+              vq[g] = V[ix[g] * LD + qq[g]];
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < GV; ++g) {
+            if (t0 + g * NT < n * H) {
+              const T c = cs[kk[g]], s = cs[H + kk[g]];
+              V[ix[g] * LD + pp[g]] = c * vp[g] - s * vq[g];
+              V[ix[g] * LD + qq[g]] = s * vp[g] + c * vq[g];
+            }
+          }
         }
       }
       gsync<NT>();
@@ -404,6 +444,7 @@ template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
 __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
   static_assert(n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
+  constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;  // as in jacobi_sym
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
     const int o = (e / n) * LD + (e % n);
@@ -429,7 +470,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
       }
     }
     off = gsum<NT>(off, red);
-    if (off <= T(JacobiTol<T>::rel2) * nrm) break;
+    if (off <= T(JacobiStop<T, n>::rel2) * nrm) break;
     for (int r = 0; r < n - 1; ++r) {
       // the rotation of each pair, and the pair's own 2x2 block made (real) diagonal
       for (int k = tid; k < H; k += NT) {
@@ -456,69 +497,102 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
       gsync<NT>();
       // the blocks (k1, k2), k1 < k2 (pairs of a circle ordering of the H pair indices), and
       // their conjugate transposes (k2, k1)
-      for (int b = tid; b < H * (H - 1) / 2; b += NT) {
-        int k1, k2;
-        rr_pair(H, b / (H / 2), b % (H / 2), k1, k2);
-        int p1, q1, p2, q2;
-        rr_pair(n, r, k1, p1, q1);
-        rr_pair(n, r, k2, p2, q2);
-        const T c1 = cs[k1], s1 = cs[H + k1], w1r = cs[2 * H + k1], w1i = cs[3 * H + k1];
-        const T c2 = cs[k2], s2 = cs[H + k2], w2r = cs[2 * H + k2], w2i = cs[3 * H + k2];
-        const T m11r = Ar[p1 * LD + p2], m11i = Ai[p1 * LD + p2];
-        const T m12r = Ar[p1 * LD + q2], m12i = Ai[p1 * LD + q2];
-        const T m21r = Ar[q1 * LD + p2], m21i = Ai[q1 * LD + p2];
-        const T m22r = Ar[q1 * LD + q2], m22i = Ai[q1 * LD + q2];
-        // X = M U2: col p = c2 m_p - s2 w2 m_q ; col q = s2 m_p + c2 w2 m_q
-        const T sw2r = s2 * w2r, sw2i = s2 * w2i, cw2r = c2 * w2r, cw2i = c2 * w2i;
-        const T x11r = c2 * m11r - (sw2r * m12r - sw2i * m12i);
-        const T x11i = c2 * m11i - (sw2r * m12i + sw2i * m12r);
-        const T x12r = s2 * m11r + (cw2r * m12r - cw2i * m12i);
-        const T x12i = s2 * m11i + (cw2r * m12i + cw2i * m12r);
-        const T x21r = c2 * m21r - (sw2r * m22r - sw2i * m22i);
-        const T x21i = c2 * m21i - (sw2r * m22i + sw2i * m22r);
-        const T x22r = s2 * m21r + (cw2r * m22r - cw2i * m22i);
-        const T x22i = s2 * m21i + (cw2r * m22i + cw2i * m22r);
-        // Y = U1^H X: row p = c1 x_p - s1 conj(w1) x_q ; row q = s1 x_p + c1 conj(w1) x_q
-        const T sw1r = s1 * w1r, sw1i = -s1 * w1i, cw1r = c1 * w1r, cw1i = -c1 * w1i;
-        const T y11r = c1 * x11r - (sw1r * x21r - sw1i * x21i);
-        const T y11i = c1 * x11i - (sw1r * x21i + sw1i * x21r);
-        const T y22r = s1 * x12r + (cw1r * x22r - cw1i * x22i);
-        const T y22i = s1 * x12i + (cw1r * x22i + cw1i * x22r);
-        const T y12r = c1 * x12r - (sw1r * x22r - sw1i * x22i);
-        const T y12i = c1 * x12i - (sw1r * x22i + sw1i * x22r);
-        const T y21r = s1 * x11r + (cw1r * x21r - cw1i * x21i);
-        const T y21i = s1 * x11i + (cw1r * x21i + cw1i * x21r);
-        Ar[p1 * LD + p2] = y11r;
-        Ai[p1 * LD + p2] = y11i;
-        Ar[p2 * LD + p1] = y11r;
-        Ai[p2 * LD + p1] = -y11i;
-        Ar[q1 * LD + q2] = y22r;
-        Ai[q1 * LD + q2] = y22i;
-        Ar[q2 * LD + q1] = y22r;
-        Ai[q2 * LD + q1] = -y22i;
-        Ar[p1 * LD + q2] = y12r;
-        Ai[p1 * LD + q2] = y12i;
-        Ar[q2 * LD + p1] = y12r;
-        Ai[q2 * LD + p1] = -y12i;
-        Ar[q1 * LD + p2] = y21r;
-        Ai[q1 * LD + p2] = y21i;
-        Ar[p2 * LD + q1] = y21r;
-        Ai[p2 * LD + q1] = -y21i;
+      constexpr int NB = H * (H - 1) / 2;
+      for (int b0 = tid; b0 < NB; b0 += GB * NT) {
+        int k1[GB], k2[GB], p1[GB], q1[GB], p2[GB], q2[GB];
+        T m11r[GB], m11i[GB], m12r[GB], m12i[GB], m21r[GB], m21i[GB], m22r[GB], m22i[GB];
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+          const int b = b0 + g * NT;
+          if (b < NB) {
+            rr_pair(H, b / (H / 2), b % (H / 2), k1[g], k2[g]);
+            rr_pair(n, r, k1[g], p1[g], q1[g]);
+            rr_pair(n, r, k2[g], p2[g], q2[g]);
+            m11r[g] = Ar[p1[g] * LD + p2[g]];
+            m11i[g] = Ai[p1[g] * LD + p2[g]];
+            m12r[g] = Ar[p1[g] * LD + q2[g]];
+            m12i[g] = Ai[p1[g] * LD + q2[g]];
+            m21r[g] = Ar[q1[g] * LD + p2[g]];
+            m21i[g] = Ai[q1[g] * LD + p2[g]];
+            m22r[g] = Ar[q1[g] * LD + q2[g]];
+            m22i[g] = Ai[q1[g] * LD + q2[g]];
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+          if (b0 + g * NT >= NB) continue;
+          const int a1 = k1[g], a2 = k2[g];
+          const T c1 = cs[a1], s1 = cs[H + a1], w1r = cs[2 * H + a1], w1i = cs[3 * H + a1];
+          const T c2 = cs[a2], s2 = cs[H + a2], w2r = cs[2 * H + a2], w2i = cs[3 * H + a2];
+          // X = M U2: col p = c2 m_p - s2 w2 m_q ; col q = s2 m_p + c2 w2 m_q
+          const T sw2r = s2 * w2r, sw2i = s2 * w2i, cw2r = c2 * w2r, cw2i = c2 * w2i;
+          const T x11r = c2 * m11r[g] - (sw2r * m12r[g] - sw2i * m12i[g]);
+          const T x11i = c2 * m11i[g] - (sw2r * m12i[g] + sw2i * m12r[g]);
+          const T x12r = s2 * m11r[g] + (cw2r * m12r[g] - cw2i * m12i[g]);
+          const T x12i = s2 * m11i[g] + (cw2r * m12i[g] + cw2i * m12r[g]);
+          const T x21r = c2 * m21r[g] - (sw2r * m22r[g] - sw2i * m22i[g]);
+          const T x21i = c2 * m21i[g] - (sw2r * m22i[g] + sw2i * m22r[g]);
+          const T x22r = s2 * m21r[g] + (cw2r * m22r[g] - cw2i * m22i[g]);
+          const T x22i = s2 * m21i[g] + (cw2r * m22i[g] + cw2i * m22r[g]);
+          // Y = U1^H X: row p = c1 x_p - s1 conj(w1) x_q ; row q = s1 x_p + c1 conj(w1) x_q
+          const T sw1r = s1 * w1r, sw1i = -s1 * w1i, cw1r = c1 * w1r, cw1i = -c1 * w1i;
+          const T y11r = c1 * x11r - (sw1r * x21r - sw1i * x21i);
+          const T y11i = c1 * x11i - (sw1r * x21i + sw1i * x21r);
+          const T y22r = s1 * x12r + (cw1r * x22r - cw1i * x22i);
+          const T y22i = s1 * x12i + (cw1r * x22i + cw1i * x22r);
+          const T y12r = c1 * x12r - (sw1r * x22r - sw1i * x22i);
+          const T y12i = c1 * x12i - (sw1r * x22i + sw1i * x22r);
+          const T y21r = s1 * x11r + (cw1r * x21r - cw1i * x21i);
+          const T y21i = s1 * x11i + (cw1r * x21i + cw1i * x21r);
+          const int P1 = p1[g], Q1 = q1[g], P2 = p2[g], Q2 = q2[g];
+          Ar[P1 * LD + P2] = y11r;
+          Ai[P1 * LD + P2] = y11i;
+          Ar[P2 * LD + P1] = y11r;
+          Ai[P2 * LD + P1] = -y11i;
+          Ar[Q1 * LD + Q2] = y22r;
+          Ai[Q1 * LD + Q2] = y22i;
+          Ar[Q2 * LD + Q1] = y22r;
+          Ai[Q2 * LD + Q1] = -y22i;
+          Ar[P1 * LD + Q2] = y12r;
+          Ai[P1 * LD + Q2] = y12i;
+          Ar[Q2 * LD + P1] = y12r;
+          Ai[Q2 * LD + P1] = -y12i;
+          Ar[Q1 * LD + P2] = y21r;
+          Ai[Q1 * LD + P2] = y21i;
+          Ar[P2 * LD + Q1] = y21r;
+          Ai[P2 * LD + Q1] = -y21i;
+        }
       }
       if constexpr (VEC) {
-        for (int t = tid; t < n * H; t += NT) {
-          const int i = t / H, k = t % H;
-          int p, q;
-          rr_pair(n, r, k, p, q);
-          const T c = cs[k], s = cs[H + k], wr = cs[2 * H + k], wi = cs[3 * H + k];
-          const T vpr = Vr[i * LD + p], vpi = Vi[i * LD + p];
-          const T vqr = Vr[i * LD + q], vqi = Vi[i * LD + q];
-          // v_p' = c v_p - s w v_q ; v_q' = s v_p + c w v_q
-          const T wvr = wr * vqr - wi * vqi, wvi = wr * vqi + wi * vqr;
-          Vr[i * LD + p] = c * vpr - s * wvr;
-          Vi[i * LD + p] = c * vpi - s * wvi;
-          Vr[i * LD + q] = s * vpr + c * wvr;
-          Vi[i * LD + q] = s * vpi + c * wvi;
+        for (int t0 = tid; t0 < n * H; t0 += GV * NT) {
+          int ix[GV], kk[GV], pp[GV], qq[GV];
+          T vpr[GV], vpi[GV], vqr[GV], vqi[GV];
+#pragma unroll
+          for (int g = 0; g < GV; ++g) {
+            const int t = t0 + g * NT;
+            if (t < n * H) {
+              ix[g] = t / H;
+              kk[g] = t % H;
+              rr_pair(n, r, kk[g], pp[g], qq[g]);
+              vpr[g] = Vr[ix[g] * LD + pp[g]];
+              vpi[g] = Vi[ix[g] * LD + pp[g]];
+              vqr[g] = Vr[ix[g] * LD + qq[g]];
+              vqi[g] = Vi[ix[g] * LD + qq[g]];
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < GV; ++g) {
+            if (t0 + g * NT >= n * H) continue;
+            const int k = kk[g];
+            const T c = cs[k], s = cs[H + k], wr = cs[2 * H + k], wi = cs[3 * H + k];
+            // v_p' = c v_p - s w v_q ; v_q' = s v_p + c w v_q
+            const T wvr = wr * vqr[g] - wi * vqi[g], wvi = wr * vqi[g] + wi * vqr[g];
+            const int op = ix[g] * LD + pp[g], oq = ix[g] * LD + qq[g];
+            Vr[op] = c * vpr[g] - s * wvr;
+            Vi[op] = c * vpi[g] - s * wvi;
+            Vr[oq] = s * vpr[g] + c * wvr;
+            Vi[oq] = s * vpi[g] + c * wvi;
+          }
         }
       }
       gsync<NT>();

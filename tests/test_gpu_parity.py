@@ -320,13 +320,14 @@ def test_first_sweep_takes_the_canonical_members(ve):
 
 
 def test_state_roundtrip_resume_and_determinism(ve):
-    """Two handles with the same history agree bitwise.  A resume through get/set state
-    restarts the eigensolves cold (the stored eigenvectors are not part of the state), so it
-    matches an uninterrupted run to rounding, not bitwise."""
+    """Two handles with the same history agree bitwise.  A state read and set back on the same
+    handle continues bit for bit (the handle keeps the eigenvectors of its last projections as
+    the eigensolves' starting point); on a fresh handle the eigensolves restart cold, so the run
+    matches an uninterrupted one to rounding."""
     lattice, cluster = (64,), (2,)
     ham = ve.ve_ham_tfim(1, 1.0, 0.9)
-    a, b, c = (ve.ve_create(lattice, cluster, ham), ve.ve_create(lattice, cluster, ham),
-               ve.ve_create(lattice, cluster, ham))
+    a, b, c, d = (ve.ve_create(lattice, cluster, ham), ve.ve_create(lattice, cluster, ham),
+                  ve.ve_create(lattice, cluster, ham), ve.ve_create(lattice, cluster, ham))
     try:
         ve.ve_iterate(a, 40, 0.0)
         ve.ve_iterate(c, 40, 0.0)
@@ -335,13 +336,16 @@ def test_state_roundtrip_resume_and_determinism(ve):
         snap = ve.ve_get_state(b)
         ve.ve_set_state(b, snap)
         ve.ve_iterate(b, 15, 0.0)
-        assert relerr(ve.ve_get_state(b), ve.ve_get_state(a)) < 1e-12
+        np.testing.assert_array_equal(ve.ve_get_state(b), ve.ve_get_state(a))
+        ve.ve_set_state(d, snap)
+        ve.ve_iterate(d, 15, 0.0)
+        assert relerr(ve.ve_get_state(d), ve.ve_get_state(a)) < 1e-12
         with pytest.raises(ve.VEError):
             ve.ve_set_state(b, snap[:-1])
         st = ve.ve_get_status(b)
         assert st.iter == 40
     finally:
-        for x in (a, b, c):
+        for x in (a, b, c, d):
             ve.ve_destroy(x)
 
 
