@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "ve_df64.cuh"
 
 namespace ve {
@@ -327,6 +329,9 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
   // in global memory (n > 64) needs several loads in flight per thread; every block and row of a
   // round is disjoint from the others, so the reordering changes no result
   constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;
+  // a matrix in global memory in float32 / double-float words takes the row-block form of the
+  // two-sided update (see below); float64 keeps the symmetric form, its pipe is the bound
+  constexpr bool ROWS = n > 64 && !std::is_same<T, double>::value;
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
     const T a = A[(e / n) * LD + (e % n)];
@@ -365,7 +370,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
         A[q * LD + p] = T(0);
       }
       gsync<NT>();
-      if constexpr (H >= 2) {
+      if constexpr (H >= 2 && !ROWS) {
         // the blocks (k1, k2), k1 < k2 -- enumerated as the pairs of a circle ordering of the
         // H pair indices -- and their transposes (k2, k1)
         constexpr int NB = H * (H - 1) / 2;
@@ -401,6 +406,45 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
               A[p2[g] * LD + q1[g]] = y21;
               A[q1[g] * LD + q2[g]] = y22;
               A[q2[g] * LD + q1[g]] = y22;
+            }
+          }
+        }
+      } else if constexpr (H >= 2) {
+        // row-block form: warp w takes the row blocks k1 = w, w + NW, ... and its lanes the
+        // column blocks k2, so the four entries of a block lie in two rows the warp reads and
+        // writes contiguously; every block k1 != k2 is transformed and none mirrored (twice the
+        // arithmetic of the symmetric form for a fraction of its scattered L2 sectors)
+        constexpr int NW = NT / 32;
+        const int w = tid >> 5, lane = tid & 31;
+        for (int k1 = w; k1 < H; k1 += NW) {
+          int p1, q1;
+          rr_pair(n, r, k1, p1, q1);
+          const T c1 = cs[k1], s1 = cs[H + k1];
+          for (int k0 = 0; k0 < H; k0 += 32 * GB) {
+            int k2[GB], p2[GB], q2[GB];
+            T m11[GB], m12[GB], m21[GB], m22[GB];
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+              k2[g] = k0 + lane + 32 * g;
+              if (k2[g] < H && k2[g] != k1) {
+                rr_pair(n, r, k2[g], p2[g], q2[g]);
+                m11[g] = A[p1 * LD + p2[g]];
+                m12[g] = A[p1 * LD + q2[g]];
+                m21[g] = A[q1 * LD + p2[g]];
+                m22[g] = A[q1 * LD + q2[g]];
+              }
+            }
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+              if (k2[g] < H && k2[g] != k1) {
+                const T c2 = cs[k2[g]], s2 = cs[H + k2[g]];
+                const T x11 = c2 * m11[g] - s2 * m12[g], x12 = s2 * m11[g] + c2 * m12[g];
+                const T x21 = c2 * m21[g] - s2 * m22[g], x22 = s2 * m21[g] + c2 * m22[g];
+                A[p1 * LD + p2[g]] = c1 * x11 - s1 * x21;
+                A[p1 * LD + q2[g]] = c1 * x12 - s1 * x22;
+                A[q1 * LD + p2[g]] = s1 * x11 + c1 * x21;
+                A[q1 * LD + q2[g]] = s1 * x12 + c1 * x22;
+              }
             }
           }
         }
@@ -445,6 +489,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
   static_assert(n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;  // as in jacobi_sym
+  constexpr bool ROWS = n > 64 && !std::is_same<T, double>::value;
   T nrm = T(0);
   for (int e = tid; e < n * n; e += NT) {
     const int o = (e / n) * LD + (e % n);
@@ -495,6 +540,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
         Ai[q * LD + p] = T(0);
       }
       gsync<NT>();
+      if constexpr (!ROWS) {
       // the blocks (k1, k2), k1 < k2 (pairs of a circle ordering of the H pair indices), and
       // their conjugate transposes (k2, k1)
       constexpr int NB = H * (H - 1) / 2;
@@ -561,6 +607,61 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
           Ai[Q1 * LD + P2] = y21i;
           Ar[P2 * LD + Q1] = y21r;
           Ai[P2 * LD + Q1] = -y21i;
+        }
+      }
+      } else {
+        // row-block form, as in jacobi_sym
+        constexpr int NW = NT / 32;
+        const int w = tid >> 5, lane = tid & 31;
+        for (int k1 = w; k1 < H; k1 += NW) {
+          int p1, q1;
+          rr_pair(n, r, k1, p1, q1);
+          const T c1 = cs[k1], s1 = cs[H + k1], w1r = cs[2 * H + k1], w1i = cs[3 * H + k1];
+          const T sw1r = s1 * w1r, sw1i = -s1 * w1i, cw1r = c1 * w1r, cw1i = -c1 * w1i;
+          for (int k0 = 0; k0 < H; k0 += 32 * GB) {
+            int k2[GB], p2[GB], q2[GB];
+            T m11r[GB], m11i[GB], m12r[GB], m12i[GB], m21r[GB], m21i[GB], m22r[GB], m22i[GB];
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+              k2[g] = k0 + lane + 32 * g;
+              if (k2[g] < H && k2[g] != k1) {
+                rr_pair(n, r, k2[g], p2[g], q2[g]);
+                m11r[g] = Ar[p1 * LD + p2[g]];
+                m11i[g] = Ai[p1 * LD + p2[g]];
+                m12r[g] = Ar[p1 * LD + q2[g]];
+                m12i[g] = Ai[p1 * LD + q2[g]];
+                m21r[g] = Ar[q1 * LD + p2[g]];
+                m21i[g] = Ai[q1 * LD + p2[g]];
+                m22r[g] = Ar[q1 * LD + q2[g]];
+                m22i[g] = Ai[q1 * LD + q2[g]];
+              }
+            }
+#pragma unroll
+            for (int g = 0; g < GB; ++g) {
+              if (k2[g] >= H || k2[g] == k1) continue;
+              const int a2 = k2[g];
+              const T c2 = cs[a2], s2 = cs[H + a2], w2r = cs[2 * H + a2], w2i = cs[3 * H + a2];
+              // X = M U2, then Y = U1^H X (as in the symmetric form)
+              const T sw2r = s2 * w2r, sw2i = s2 * w2i, cw2r = c2 * w2r, cw2i = c2 * w2i;
+              const T x11r = c2 * m11r[g] - (sw2r * m12r[g] - sw2i * m12i[g]);
+              const T x11i = c2 * m11i[g] - (sw2r * m12i[g] + sw2i * m12r[g]);
+              const T x12r = s2 * m11r[g] + (cw2r * m12r[g] - cw2i * m12i[g]);
+              const T x12i = s2 * m11i[g] + (cw2r * m12i[g] + cw2i * m12r[g]);
+              const T x21r = c2 * m21r[g] - (sw2r * m22r[g] - sw2i * m22i[g]);
+              const T x21i = c2 * m21i[g] - (sw2r * m22i[g] + sw2i * m22r[g]);
+              const T x22r = s2 * m21r[g] + (cw2r * m22r[g] - cw2i * m22i[g]);
+              const T x22i = s2 * m21i[g] + (cw2r * m22i[g] + cw2i * m22r[g]);
+              const int P2 = p2[g], Q2 = q2[g];
+              Ar[p1 * LD + P2] = c1 * x11r - (sw1r * x21r - sw1i * x21i);
+              Ai[p1 * LD + P2] = c1 * x11i - (sw1r * x21i + sw1i * x21r);
+              Ar[q1 * LD + Q2] = s1 * x12r + (cw1r * x22r - cw1i * x22i);
+              Ai[q1 * LD + Q2] = s1 * x12i + (cw1r * x22i + cw1i * x22r);
+              Ar[p1 * LD + Q2] = c1 * x12r - (sw1r * x22r - sw1i * x22i);
+              Ai[p1 * LD + Q2] = c1 * x12i - (sw1r * x22i + sw1i * x22r);
+              Ar[q1 * LD + P2] = s1 * x11r + (cw1r * x21r - cw1i * x21i);
+              Ai[q1 * LD + P2] = s1 * x11i + (cw1r * x21i + cw1i * x21r);
+            }
+          }
         }
       }
       if constexpr (VEC) {
