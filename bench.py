@@ -565,17 +565,78 @@ def run_batch(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2106_02682_gb300 import synth, ve
-    prec = ve.VE_PREC_FP64 if args.precision == "fp64" else ve.VE_PREC_MIXED
+    prec = {"fp64": ve.VE_PREC_FP64, "mixed": ve.VE_PREC_MIXED, "df64": ve.VE_PREC_DF64}[args.precision]
     fam = args.workload.split("_", 1)[1]
     count = 256 if fam == "c4" else 64
     r = batch_rate(ve, synth, fam, count, args.steps, prec)
     print(json.dumps({"metric": METRIC, "value": r["batched_instance_sweeps_per_s"],
                       "unit": "instance-sweeps/s", "n_gpus": 1, "steps": args.steps,
                       "warmup": 3, "higher_is_better": True, "scaling": "weak",
-                      "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32+f64",
+                      "vs_baseline": None, "dtype": {0: "f64", 1: "f32+f32x2", 2: "f32x2"}[prec],
                       "data": "synthetic", "config": {"workload": args.workload, **r},
                       "timing": "wall clock around ve_batch_iterate / ve_iterate, no L2 flush"}),
           flush=True)
+
+
+PROJ_WORKLOADS = {"proj512_b455": (512, 455)}
+
+
+def run_projection(args):
+    """Kernel-only batched PSD projection: 455 real symmetric 512 x 512 matrices (a 64 x 64
+    lattice's worth of 3 x 3 clusters, restated as a projection benchmark), float64 in and out,
+    through ve_project_psd_sym_large.  Each step projects the whole batch (0.95 GB of input,
+    larger than L2); CUDA events on the launching stream."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02682_gb300 import synth, ve
+    n, count = PROJ_WORKLOADS[args.workload]
+    prec = {"fp64": ve.VE_PREC_FP64, "mixed": ve.VE_PREC_MIXED, "df64": ve.VE_PREC_DF64}[args.precision]
+    steps, warmup = min(args.steps, 3), min(args.warmup, 1)
+    A = synth.symmetric_batch(count, n, seed=20210604)
+    x = torch.from_numpy(A).cuda()
+    y = torch.empty_like(x)
+    ws_bytes = ve.ve_project_psd_large_workspace_size(n, False, prec)
+    ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def project():
+        ve.ve_project_psd_sym_large(x.data_ptr(), y.data_ptr(), n, count, ws.data_ptr(), ws_bytes,
+                                    prec, stream.cuda_stream)
+
+    for _ in range(warmup):
+        project()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    clocks = ClockSampler(0)
+    for a, b in ev:
+        a.record(stream)
+        project()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    value = count * steps / (ms * 1e-3)
+    # the oracle's projection (numpy eigh) on a sample of the same matrices
+    from oracle import ve_oracle as vo
+    sample = 16
+    t0, c0 = time.perf_counter(), time.process_time()
+    vo.proj_psd(A[:sample])
+    el = time.perf_counter() - t0
+    cores = round((time.process_time() - c0) / el, 2)
+    print(json.dumps({
+        "metric": "batched PSD projection of 512 x 512 real symmetric matrices", "value": value,
+        "unit": "matrices/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "f64", 1: "f32", 2: "f32x2"}[prec],
+        "data": "synthetic (random symmetric, every 7th with eigenvalues +1/-1/0 repeated)",
+        "config": {"workload": args.workload, "n": n, "batch": count,
+                   "workspace_bytes": ws_bytes, "l2": "inputs 0.95 GB, larger than L2"},
+        "gpu_launches": steps, "clocks": ck,
+        "cpu_baseline": {"value": sample / el, "unit": "matrices/s", "cores": cores,
+                         "kind": "oracle", "sample": f"{sample} matrices, numpy eigh + clip"}}),
+        flush=True)
 
 
 def main():
@@ -584,6 +645,8 @@ def main():
         run_reference(args)
     elif args.workload.startswith("batch_"):
         run_batch(args)
+    elif args.workload in PROJ_WORKLOADS:
+        run_projection(args)
     else:
         run_ours(args)
 

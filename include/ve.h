@@ -251,6 +251,21 @@ int ve_project_psd_sym(const double* in, double* out, int n, long count, int pre
 int ve_project_psd_herm(const double* in, double* out, int n, long count, int precision,
                         void* stream);
 
+/* The same projections for larger matrices: real symmetric n in {256, 512}, complex Hermitian
+ * n = 256 (the per-wavevector blocks of 2 x 2 clusters, Algorithm 6).  Each matrix is staged
+ * in a per-SM slice of `workspace` (device memory owned by the caller, 256-byte aligned, at
+ * least ve_project_psd_large_workspace_size(n, hermitian, precision) bytes -- that size is
+ * for the current device); one CTA per SM runs a cyclic Jacobi eigensolve from V = I.
+ * Layout as above (in == out allowed).  Calls sharing a workspace must not overlap on the GPU.
+ * ve_project_psd_large_workspace_size returns 0 for an unsupported n or precision.
+ * Errors: VE_EINVAL (n, count < 0, precision, workspace missing, small or misaligned),
+ * VE_ECUDA. */
+size_t ve_project_psd_large_workspace_size(int n, int hermitian, int precision);
+int ve_project_psd_sym_large(const double* in, double* out, int n, long count, int precision,
+                             void* workspace, size_t workspace_bytes, void* stream);
+int ve_project_psd_herm_large(const double* in, double* out, int n, long count, int precision,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
 /* The global X step of Algorithm 6 on a first block row, without the G term: given X'_{0,delta}
  * (N blocks D x D, device, N = M0*M1 clusters of a dim-1 or dim-2 cluster lattice with M[p]
  * clusters per axis), write X_{0,delta} = (1/N) sum_k e^{+i 2 pi delta.k/M} Pi_{>=0}(C_k),

@@ -874,6 +874,38 @@ int ve_project_psd_herm(const double* in, double* out, int n, long count, int pr
   return VE_OK;
 }
 
+size_t ve_project_psd_large_workspace_size(int n, int hermitian, int precision) {
+  if (precision != VE_PREC_FP64 && precision != VE_PREC_MIXED && precision != VE_PREC_DF64)
+    return 0;
+  return proj_ws_bytes(n, hermitian != 0, precision_arith(precision));
+}
+
+static int project_large(const double* in, double* out, int n, long count, int precision,
+                         void* workspace, size_t workspace_bytes, void* stream, bool herm) {
+  cudaGetLastError();  // report only errors raised by this call
+  if (!in || !out || !workspace || count < 0) return VE_EINVAL;
+  const size_t need = ve_project_psd_large_workspace_size(n, herm ? 1 : 0, precision);
+  if (need == 0 || workspace_bytes < need || ((uintptr_t)workspace) % kAlign) return VE_EINVAL;
+  const int arith = precision_arith(precision);
+  unsigned char* ws = (unsigned char*)workspace;
+  if (herm) {
+    VE_CU(launch_proj_herm(in, out, n, count, arith, (cudaStream_t)stream, ws));
+  } else {
+    VE_CU(launch_proj_sym(in, out, n, count, arith, (cudaStream_t)stream, ws));
+  }
+  return VE_OK;
+}
+
+int ve_project_psd_sym_large(const double* in, double* out, int n, long count, int precision,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+  return project_large(in, out, n, count, precision, workspace, workspace_bytes, stream, false);
+}
+
+int ve_project_psd_herm_large(const double* in, double* out, int n, long count, int precision,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  return project_large(in, out, n, count, precision, workspace, workspace_bytes, stream, true);
+}
+
 size_t ve_circulant_workspace_size(int dim, const int M[2], int D) {
   if (!M || D == 256) return 0;
   FftPlan p;

@@ -120,21 +120,25 @@ __global__ void __launch_bounds__(256) k_bound_k0(const BoundArgs a) {
 }
 
 // ---------------------------------------------------------------- standalone projections
+// n <= 64: the matrices are staged in shared memory; n = 256, 512: in a per-CTA slice of a
+// caller workspace (one CTA of 512 threads per SM), as the D = 256 solver kernels do.
 template <int n, typename T>
 struct PShape {
   static constexpr int NT = GroupShape<n>::NT, LD = GroupShape<n>::LD;
+  static constexpr bool G = GroupShape<n>::GLOBAL;
   static constexpr int GPC = (NT == 32) ? 4 : 1;
   static constexpr size_t MAT = ((sizeof(T) * n * LD + 15) / 16) * 16;
-  static constexpr size_t bytes = 4 * MAT + sizeof(T) * (3 * n + 16);
+  static constexpr size_t bytes = ((4 * MAT + sizeof(T) * (3 * n + 16) + 255) / 256) * 256;
 };
 
 template <int n, typename T>
 __global__ void __launch_bounds__(PShape<n, T>::NT * PShape<n, T>::GPC)
-    k_proj_sym(const double* in, double* out, long count) {
+    k_proj_sym(const double* in, double* out, long count, unsigned char* gws) {
   constexpr int NT = PShape<n, T>::NT, LD = PShape<n, T>::LD, GPC = PShape<n, T>::GPC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
-  unsigned char* base = smem_raw + (size_t)g * PShape<n, T>::bytes;
+  unsigned char* base = PShape<n, T>::G ? gws + (size_t)blockIdx.x * PShape<n, T>::bytes
+                                        : smem_raw + (size_t)g * PShape<n, T>::bytes;
   T* A = reinterpret_cast<T*>(base);
   T* V = reinterpret_cast<T*>(base + PShape<n, T>::MAT);
   T* cs = reinterpret_cast<T*>(base + 4 * PShape<n, T>::MAT);
@@ -158,11 +162,24 @@ __global__ void __launch_bounds__(PShape<n, T>::NT * PShape<n, T>::GPC)
     }
     gsync<NT>();
     double* O = out + b * n * n;
-    for (int e = tid; e < n * n; e += NT) {
-      const int i = e / n, j = e % n;
-      T s = T(0);
-      for (int k = 0; k < n; ++k) s += W[k] * V[i * LD + k] * V[j * LD + k];
-      O[e] = (double)s;
+    if constexpr (PShape<n, T>::G) {
+      // V^T into A's storage, then the output row by row with the lanes along j, so that
+      // V^T[k][j] is read contiguously and V^T[k][i] is the same for the whole warp
+      for (int e = tid; e < n * n; e += NT) A[(e % n) * LD + e / n] = V[(e / n) * LD + e % n];
+      gsync<NT>();
+      for (int e = tid; e < n * n; e += NT) {
+        const int i = e / n, j = e % n;
+        T s = T(0);
+        for (int k = 0; k < n; ++k) s += W[k] * A[k * LD + i] * A[k * LD + j];
+        O[e] = (double)s;
+      }
+    } else {
+      for (int e = tid; e < n * n; e += NT) {
+        const int i = e / n, j = e % n;
+        T s = T(0);
+        for (int k = 0; k < n; ++k) s += W[k] * V[i * LD + k] * V[j * LD + k];
+        O[e] = (double)s;
+      }
     }
     gsync<NT>();
   }
@@ -170,11 +187,12 @@ __global__ void __launch_bounds__(PShape<n, T>::NT * PShape<n, T>::GPC)
 
 template <int n, typename T>
 __global__ void __launch_bounds__(PShape<n, T>::NT * PShape<n, T>::GPC)
-    k_proj_herm(const double* in, double* out, long count) {
+    k_proj_herm(const double* in, double* out, long count, unsigned char* gws) {
   constexpr int NT = PShape<n, T>::NT, LD = PShape<n, T>::LD, GPC = PShape<n, T>::GPC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
-  unsigned char* base = smem_raw + (size_t)g * PShape<n, T>::bytes;
+  unsigned char* base = PShape<n, T>::G ? gws + (size_t)blockIdx.x * PShape<n, T>::bytes
+                                        : smem_raw + (size_t)g * PShape<n, T>::bytes;
   T* Ar = reinterpret_cast<T*>(base);
   T* Ai = reinterpret_cast<T*>(base + PShape<n, T>::MAT);
   T* Vr = reinterpret_cast<T*>(base + 2 * PShape<n, T>::MAT);
@@ -206,13 +224,31 @@ __global__ void __launch_bounds__(PShape<n, T>::NT * PShape<n, T>::GPC)
     }
     gsync<NT>();
     double* O = out + b * n * n * 2;
+    // n > 64: V^T into (Ar, Ai) first (see k_proj_sym), so the lanes read along rows
+    if constexpr (PShape<n, T>::G) {
+      for (int e = tid; e < n * n; e += NT) {
+        Ar[(e % n) * LD + e / n] = Vr[(e / n) * LD + e % n];
+        Ai[(e % n) * LD + e / n] = Vi[(e / n) * LD + e % n];
+      }
+      gsync<NT>();
+    }
     for (int e = tid; e < n * n; e += NT) {
       const int i = e / n, j = e % n;
       T yr = T(0), yi = T(0);
       for (int k = 0; k < n; ++k) {
         const T w = W[k];
-        const T air = Vr[i * LD + k], aii = Vi[i * LD + k];
-        const T ajr = Vr[j * LD + k], aji = Vi[j * LD + k];
+        T air, aii, ajr, aji;
+        if constexpr (PShape<n, T>::G) {
+          air = Ar[k * LD + i];
+          aii = Ai[k * LD + i];
+          ajr = Ar[k * LD + j];
+          aji = Ai[k * LD + j];
+        } else {
+          air = Vr[i * LD + k];
+          aii = Vi[i * LD + k];
+          ajr = Vr[j * LD + k];
+          aji = Vi[j * LD + k];
+        }
         yr += w * (air * ajr + aii * aji);
         yi += w * (aii * ajr - air * aji);
       }
@@ -247,28 +283,42 @@ cudaError_t launch_bound_t(const BoundArgs& a, cudaStream_t s) {
 }
 
 template <int n, typename T>
-cudaError_t launch_proj_sym_t(const double* in, double* out, long count, cudaStream_t s) {
+cudaError_t launch_proj_sym_t(const double* in, double* out, long count, unsigned char* gws,
+                              cudaStream_t s) {
   using S = PShape<n, T>;
-  const size_t smem = S::bytes * S::GPC;
-  static unsigned long long mask = 0;
-  cudaError_t e = smem_once(k_proj_sym<n, T>, smem, mask);
-  if (e != cudaSuccess) return e;
   long blocks = (count + S::GPC - 1) / S::GPC;
   if (blocks > 65535L * 8) blocks = 65535L * 8;
-  k_proj_sym<n, T><<<(unsigned)blocks, S::NT * S::GPC, smem, s>>>(in, out, count);
+  if constexpr (S::G) {
+    if (!gws) return cudaErrorInvalidValue;
+    if (blocks > big_grid()) blocks = big_grid();
+    k_proj_sym<n, T><<<(unsigned)blocks, S::NT, 0, s>>>(in, out, count, gws);
+  } else {
+    const size_t smem = S::bytes * S::GPC;
+    static unsigned long long mask = 0;
+    cudaError_t e = smem_once(k_proj_sym<n, T>, smem, mask);
+    if (e != cudaSuccess) return e;
+    k_proj_sym<n, T><<<(unsigned)blocks, S::NT * S::GPC, smem, s>>>(in, out, count, nullptr);
+  }
   return cudaGetLastError();
 }
 
 template <int n, typename T>
-cudaError_t launch_proj_herm_t(const double* in, double* out, long count, cudaStream_t s) {
+cudaError_t launch_proj_herm_t(const double* in, double* out, long count, unsigned char* gws,
+                               cudaStream_t s) {
   using S = PShape<n, T>;
-  const size_t smem = S::bytes * S::GPC;
-  static unsigned long long mask = 0;
-  cudaError_t e = smem_once(k_proj_herm<n, T>, smem, mask);
-  if (e != cudaSuccess) return e;
   long blocks = (count + S::GPC - 1) / S::GPC;
   if (blocks > 65535L * 8) blocks = 65535L * 8;
-  k_proj_herm<n, T><<<(unsigned)blocks, S::NT * S::GPC, smem, s>>>(in, out, count);
+  if constexpr (S::G) {
+    if (!gws) return cudaErrorInvalidValue;
+    if (blocks > big_grid()) blocks = big_grid();
+    k_proj_herm<n, T><<<(unsigned)blocks, S::NT, 0, s>>>(in, out, count, gws);
+  } else {
+    const size_t smem = S::bytes * S::GPC;
+    static unsigned long long mask = 0;
+    cudaError_t e = smem_once(k_proj_herm<n, T>, smem, mask);
+    if (e != cudaSuccess) return e;
+    k_proj_herm<n, T><<<(unsigned)blocks, S::NT * S::GPC, smem, s>>>(in, out, count, nullptr);
+  }
   return cudaGetLastError();
 }
 
@@ -287,47 +337,67 @@ cudaError_t launch_bound(const BoundArgs& a, cudaStream_t s) {
 size_t bound_ws_bytes(int D) { return D == 256 ? BShape<256>::bytes * (size_t)big_grid() : 0; }
 
 template <int n>
-cudaError_t proj_sym_n(const double* in, double* out, long count, int arith, cudaStream_t s) {
+cudaError_t proj_sym_n(const double* in, double* out, long count, int arith, unsigned char* gws,
+                       cudaStream_t s) {
   switch (arith) {
-    case ARITH_FP64: return launch_proj_sym_t<n, double>(in, out, count, s);
-    case ARITH_FP32: return launch_proj_sym_t<n, float>(in, out, count, s);
-    case ARITH_DF64: return launch_proj_sym_t<n, df64>(in, out, count, s);
+    case ARITH_FP64: return launch_proj_sym_t<n, double>(in, out, count, gws, s);
+    case ARITH_FP32: return launch_proj_sym_t<n, float>(in, out, count, gws, s);
+    case ARITH_DF64: return launch_proj_sym_t<n, df64>(in, out, count, gws, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int n>
-cudaError_t proj_herm_n(const double* in, double* out, long count, int arith, cudaStream_t s) {
+cudaError_t proj_herm_n(const double* in, double* out, long count, int arith, unsigned char* gws,
+                        cudaStream_t s) {
   switch (arith) {
-    case ARITH_FP64: return launch_proj_herm_t<n, double>(in, out, count, s);
-    case ARITH_FP32: return launch_proj_herm_t<n, float>(in, out, count, s);
-    case ARITH_DF64: return launch_proj_herm_t<n, df64>(in, out, count, s);
+    case ARITH_FP64: return launch_proj_herm_t<n, double>(in, out, count, gws, s);
+    case ARITH_FP32: return launch_proj_herm_t<n, float>(in, out, count, gws, s);
+    case ARITH_DF64: return launch_proj_herm_t<n, df64>(in, out, count, gws, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, int arith,
-                            cudaStream_t s) {
+                            cudaStream_t s, unsigned char* gws) {
   if (count == 0) return cudaSuccess;
   switch (n) {
-    case 2: return proj_sym_n<2>(in, out, count, arith, s);
-    case 4: return proj_sym_n<4>(in, out, count, arith, s);
-    case 8: return proj_sym_n<8>(in, out, count, arith, s);
-    case 16: return proj_sym_n<16>(in, out, count, arith, s);
-    case 64: return proj_sym_n<64>(in, out, count, arith, s);
+    case 2: return proj_sym_n<2>(in, out, count, arith, nullptr, s);
+    case 4: return proj_sym_n<4>(in, out, count, arith, nullptr, s);
+    case 8: return proj_sym_n<8>(in, out, count, arith, nullptr, s);
+    case 16: return proj_sym_n<16>(in, out, count, arith, nullptr, s);
+    case 64: return proj_sym_n<64>(in, out, count, arith, nullptr, s);
+    case 256: return proj_sym_n<256>(in, out, count, arith, gws, s);
+    case 512: return proj_sym_n<512>(in, out, count, arith, gws, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_proj_herm(const double* in, double* out, int n, long count, int arith,
-                             cudaStream_t s) {
+                             cudaStream_t s, unsigned char* gws) {
   if (count == 0) return cudaSuccess;
   switch (n) {
-    case 4: return proj_herm_n<4>(in, out, count, arith, s);
-    case 16: return proj_herm_n<16>(in, out, count, arith, s);
-    case 64: return proj_herm_n<64>(in, out, count, arith, s);
+    case 4: return proj_herm_n<4>(in, out, count, arith, nullptr, s);
+    case 16: return proj_herm_n<16>(in, out, count, arith, nullptr, s);
+    case 64: return proj_herm_n<64>(in, out, count, arith, nullptr, s);
+    case 256: return proj_herm_n<256>(in, out, count, arith, gws, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+size_t proj_ws_bytes(int n, bool herm, int arith) {
+  size_t per = 0;
+  if (herm) {
+    if (n != 256) return 0;
+    per = arith == ARITH_FP32 ? PShape<256, float>::bytes : PShape<256, double>::bytes;
+  } else if (n == 256) {
+    per = arith == ARITH_FP32 ? PShape<256, float>::bytes : PShape<256, double>::bytes;
+  } else if (n == 512) {
+    per = arith == ARITH_FP32 ? PShape<512, float>::bytes : PShape<512, double>::bytes;
+  } else {
+    return 0;
+  }
+  return per * (size_t)big_grid();
 }
 
 }  // namespace ve

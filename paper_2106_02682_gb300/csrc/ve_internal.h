@@ -155,9 +155,12 @@ struct BoundArgs {
 cudaError_t launch_bound(const BoundArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------ standalone projections
+// Standalone batched projections; n = 256, 512 (Hermitian: 256) stage each matrix in a
+// per-CTA slice of gws (proj_ws_bytes), smaller n ignore it.
 cudaError_t launch_proj_sym(const double* in, double* out, int n, long count, int arith,
-                            cudaStream_t s);
+                            cudaStream_t s, unsigned char* gws = nullptr);
 cudaError_t launch_proj_herm(const double* in, double* out, int n, long count, int arith,
-                             cudaStream_t s);
+                             cudaStream_t s, unsigned char* gws = nullptr);
+size_t proj_ws_bytes(int n, bool herm, int arith);
 
 }  // namespace ve

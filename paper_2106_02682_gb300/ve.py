@@ -121,6 +121,11 @@ def _load():
         "ve_mlp_predict": (c_int, [c_void_p, P_float, c_int, P_float]),
         "ve_project_psd_sym": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
         "ve_project_psd_herm": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p]),
+        "ve_project_psd_large_workspace_size": (c_size_t, [c_int, c_int, c_int]),
+        "ve_project_psd_sym_large": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p,
+                                             c_size_t, c_void_p]),
+        "ve_project_psd_herm_large": (c_int, [c_void_p, c_void_p, c_int, c_long, c_int, c_void_p,
+                                              c_size_t, c_void_p]),
         "ve_circulant_workspace_size": (c_size_t, [c_int, ctypes.POINTER(c_int), c_int]),
         "ve_circulant_project": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(c_int), c_int,
                                          c_int, c_void_p, c_size_t, c_void_p]),
@@ -273,6 +278,24 @@ def ve_project_psd_sym(in_ptr, out_ptr, n, count, precision=VE_PREC_FP64, stream
 def ve_project_psd_herm(in_ptr, out_ptr, n, count, precision=VE_PREC_FP64, stream=None):
     return _check(_lib.ve_project_psd_herm(in_ptr, out_ptr, int(n), int(count), int(precision),
                                            stream), "ve_project_psd_herm")
+
+
+def ve_project_psd_large_workspace_size(n, hermitian=False, precision=VE_PREC_FP64):
+    return _lib.ve_project_psd_large_workspace_size(int(n), 1 if hermitian else 0, int(precision))
+
+
+def ve_project_psd_sym_large(in_ptr, out_ptr, n, count, ws_ptr, ws_bytes, precision=VE_PREC_FP64,
+                             stream=None):
+    return _check(_lib.ve_project_psd_sym_large(in_ptr, out_ptr, int(n), int(count),
+                                                int(precision), ws_ptr, int(ws_bytes), stream),
+                  "ve_project_psd_sym_large")
+
+
+def ve_project_psd_herm_large(in_ptr, out_ptr, n, count, ws_ptr, ws_bytes, precision=VE_PREC_FP64,
+                              stream=None):
+    return _check(_lib.ve_project_psd_herm_large(in_ptr, out_ptr, int(n), int(count),
+                                                 int(precision), ws_ptr, int(ws_bytes), stream),
+                  "ve_project_psd_herm_large")
 
 
 def _M(M):

@@ -118,6 +118,41 @@ def test_projection_degenerate_cases(ve):
         assert np.max(np.abs(out[b] - ref[b])) <= RTOL64 * max(1.0, np.max(np.abs(A[b]))), b
 
 
+@pytest.mark.parametrize("n,herm", [(256, False), (512, False), (256, True)])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_large_projection_matches_oracle(ve, n, herm, prec):
+    """n = 256, 512 staged in a caller workspace (the 4-spin-cluster blocks, and the kernel-only
+    512 x 512 batch); the first matrix of each batch has eigenvalues +1, -1, 0 repeated."""
+    count = 3 if n == 256 else 2
+    A = (synth.hermitian_batch(count, n, seed=n + 11) if herm
+         else synth.symmetric_batch(count, n, seed=n + 5))
+    host = np.stack([A.real, A.imag], axis=-1) if herm else A
+    x = dev(host)
+    y = torch.empty_like(x)
+    ws_bytes = ve.ve_project_psd_large_workspace_size(n, herm, prec)
+    assert ws_bytes > 0
+    ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.float64, device="cuda")
+    fn = ve.ve_project_psd_herm_large if herm else ve.ve_project_psd_sym_large
+    fn(x.data_ptr(), y.data_ptr(), n, count, ws.data_ptr(), ws_bytes, prec)
+    torch.cuda.synchronize()
+    o = y.cpu().numpy()
+    out = o[..., 0] + 1j * o[..., 1] if herm else o
+    ref = vo.proj_psd(A)
+    for b in range(count):
+        if prec == 1:
+            tol = tol32(A[b])
+        else:
+            tol = state_tol(prec) * (n / 64.0) * max(1.0, np.max(np.abs(A[b])))
+        assert np.max(np.abs(out[b] - ref[b])) <= tol, (b, np.max(np.abs(out[b] - ref[b])), tol)
+    # in place, an empty batch, and a workspace one byte short
+    fn(x.data_ptr(), x.data_ptr(), n, count, ws.data_ptr(), ws_bytes, prec)
+    fn(x.data_ptr(), x.data_ptr(), n, 0, ws.data_ptr(), ws_bytes, prec)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.cpu().numpy(), o)
+    with pytest.raises(ve.VEError):
+        fn(x.data_ptr(), y.data_ptr(), n, count, ws.data_ptr(), ws_bytes - 1, prec)
+
+
 # ------------------------------------------------------------------ S7-S9: the X step
 
 CIRC = [((2,), 4), ((3,), 16), ((5,), 4), ((6,), 16), ((16,), 16), ((50,), 16), ((64,), 16),
