@@ -318,11 +318,89 @@ __device__ __forceinline__ void unit_phase<df64>(df64 br, df64 bi, df64& mag, df
   mag = ldexp_df(q * y, isc);
 }
 
+// Early stop with a first-order correction (Daleckii-Krein).  With A = Lambda + E (Lambda its
+// diagonal) and f(x) = max(x, 0), f(A) = f(Lambda) + L o E + R, L_ij the divided difference
+// (f(l_i) - f(l_j)) / (l_i - l_j) (1 between two non-negative diagonal entries, 0 between two
+// negative ones, l_+ / (l_+ - l_-) across zero).  While the spectrum of Lambda + t E stays clear
+// of zero, f is linear on either side of it and the remainder is of second order, governed by
+// the distance d of the diagonal from zero: ||R||_F <= c ||E||_F^2 / d (c well below 1 over
+// random 16 x 16 tests).  The sweeps may stop once ||E||_F^2 <= n u ||A||_F d -- as accurate as
+// the exact stopping rule -- provided also ||E||_F <= d / 4, so that no eigenvalue can reach
+// zero.  `off` and `nrm` are the squared Frobenius norms of E and A; the test is uniform over
+// the group.
+template <typename T, int n, int LD, int NT>
+__device__ bool dk_stop(const T* A, T off, T nrm, T* red, int tid) {
+  T d = T(1e30f);
+  for (int k = tid; k < n; k += NT) d = fmin(d, fabs(A[k * LD + k]));
+  d = gmin<NT>(d, red);
+  return off * off <= T(JacobiStop<T, n>::rel2) * nrm * d * d && T(16) * off <= d * d;
+}
+
+// 1 / x for x > 0 without a float64 divide: power-of-two scaling, float32 seed, two Newton steps.
+template <typename T>
+__device__ __forceinline__ T recip_pos(T x) {
+  return T(1) / x;
+}
+template <>
+__device__ __forceinline__ double recip_pos<double>(double x) {
+  const double sc = pow2_inverse_scale(x);
+  const double xs = x * sc;  // in [1, 2)
+  double r = (double)__frcp_rn((float)xs);
+  r = r * fma(-xs, r, 2.0);
+  r = r * fma(-xs, r, 2.0);
+  return r * sc;
+}
+
+// The weight L_ij of dk_stop for the diagonal entries l_i, l_j.
+template <typename T>
+__device__ __forceinline__ T dk_weight(T li, T lj) {
+  const bool pi = li >= T(0), pj = lj >= T(0);
+  if (pi && pj) return T(1);
+  if (!pi && !pj) return T(0);
+  const T lp = pi ? li : lj, lm = pi ? lj : li;  // lp >= 0 > lm
+  return lp * recip_pos<T>(lp - lm);
+}
+
+// M = f(Lambda) + L o E in place of A after an early stop (the eigenvalue estimates go to lam,
+// n entries); the projection is then V M V^T (V M V^H).
+template <typename T, int n, int LD, int NT>
+__device__ void dk_matrix_sym(T* A, T* lam, int tid) {
+  for (int k = tid; k < n; k += NT) lam[k] = A[k * LD + k];
+  gsync<NT>();
+  for (int e = tid; e < n * n; e += NT) {
+    const int i = e / n, j = e % n;
+    const T li = lam[i];
+    A[i * LD + j] = (i == j) ? (li > T(0) ? li : T(0)) : A[i * LD + j] * dk_weight<T>(li, lam[j]);
+  }
+  gsync<NT>();
+}
+
+template <typename T, int n, int LD, int NT>
+__device__ void dk_matrix_herm(T* Ar, T* Ai, T* lam, int tid) {
+  for (int k = tid; k < n; k += NT) lam[k] = Ar[k * LD + k];
+  gsync<NT>();
+  for (int e = tid; e < n * n; e += NT) {
+    const int i = e / n, j = e % n;
+    const T li = lam[i];
+    if (i == j) {
+      Ar[i * LD + i] = li > T(0) ? li : T(0);
+      Ai[i * LD + i] = T(0);
+    } else {
+      const T w = dk_weight<T>(li, lam[j]);
+      Ar[i * LD + j] = Ar[i * LD + j] * w;
+      Ai[i * LD + j] = Ai[i * LD + j] * w;
+    }
+  }
+  gsync<NT>();
+}
+
 // Real symmetric Jacobi on A (n x n, leading dimension LD) in shared memory.  If VEC, V (same
 // layout) receives the eigenvectors.  cs: shared scratch of n entries; red: NT/32 entries.
 // Returns the number of sweeps performed.
-template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
-__device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
+// With DK the sweeps may also stop early under dk_stop; *dk then tells the caller to
+// reconstruct with the first-order correction (dk_matrix) instead of diag(max(l, 0)).
+template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
+__device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr) {
   static_assert(n == 2 || n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   // blocks (GB) and eigenvector rows (GV) a thread loads before it stores any: a matrix staged
@@ -343,6 +421,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
     for (int e = tid; e < n * n; e += NT) V[(e / n) * LD + (e % n)] = (e / n == e % n) ? T(1) : T(0);
   }
   gsync<NT>();
+  if constexpr (DK) *dk = false;
   int sweep = 0;
   for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
     T off = T(0);
@@ -355,6 +434,12 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
     }
     off = gsum<NT>(off, red);
     if (off <= T(JacobiStop<T, n>::rel2) * nrm) break;
+    if constexpr (DK) {
+      if (dk_stop<T, n, LD, NT>(A, off, nrm, red, tid)) {
+        *dk = true;
+        break;
+      }
+    }
     for (int r = 0; r < n - 1; ++r) {
       // the rotation of each pair, and the pair's own 2x2 block made diagonal
       for (int k = tid; k < H; k += NT) {
@@ -485,8 +570,8 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid) {
 // unitary U = diag(1, w) J, w = e^{-i phi}, J the real rotation of [[a_pp, |b|], [|b|, a_qq]],
 // diagonalises the 2x2 block; A <- U^H A U, V <- V U.  cs: shared scratch of 2n entries.
 // Returns the number of sweeps performed.
-template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true>
-__device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
+template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
+__device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, bool* dk = nullptr) {
   static_assert(n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;  // as in jacobi_sym (measured)
@@ -505,6 +590,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
     }
   }
   gsync<NT>();
+  if constexpr (DK) *dk = false;
   int sweep = 0;
   for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
     T off = T(0);
@@ -517,6 +603,12 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid) {
     }
     off = gsum<NT>(off, red);
     if (off <= T(JacobiStop<T, n>::rel2) * nrm) break;
+    if constexpr (DK) {
+      if (dk_stop<T, n, LD, NT>(Ar, off, nrm, red, tid)) {
+        *dk = true;
+        break;
+      }
+    }
     for (int r = 0; r < n - 1; ++r) {
       // the rotation of each pair, and the pair's own 2x2 block made (real) diagonal
       for (int k = tid; k < H; k += NT) {

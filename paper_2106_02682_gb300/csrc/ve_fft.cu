@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
     T* vr = vstore ? vstore + (long)s * 2 * D * D : nullptr;
     T* vi = vr ? vr + D * D : nullptr;
     int nsw = 0;
+    bool dk = false;  // the eigensolve stopped early: reconstruct with the first-order correction
     if (warm && vr) {
       for (int e = tid; e < D * D; e += NT) {
         Vr[(e / D) * LD + (e % D)] = vr[e];
@@ -319,9 +320,9 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
         Ai[jj * LD + i] = (i == jj) ? T(0) : -xi;
       }
       gsync<NT>();
-      nsw = jacobi_herm<T, D, LD, NT, true, false>(Ar, Ai, Vr, Vi, cs, red, tid);
+      nsw = jacobi_herm<T, D, LD, NT, true, false, true>(Ar, Ai, Vr, Vi, cs, red, tid, &dk);
     } else {
-      nsw = jacobi_herm<T, D, LD, NT, true, true>(Ar, Ai, Vr, Vi, cs, red, tid);
+      nsw = jacobi_herm<T, D, LD, NT, true, true, true>(Ar, Ai, Vr, Vi, cs, red, tid, &dk);
     }
     if (stats && tid == 0) {
       atomicAdd(stats, (unsigned long long)nsw);
@@ -333,27 +334,60 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
         vi[e] = Vi[(e / D) * LD + (e % D)];
       }
     }
-    for (int k = tid; k < D; k += NT) {
-      const T w = Ar[k * LD + k];
-      W[k] = w > T(0) ? w : T(0);
-    }
-    gsync<NT>();
-    // Y = V diag(max(w,0)) V^H, written back into (Ar, Ai)
-    for (int t = tid; t < D * (D + 1) / 2; t += NT) {
-      int i, jj;
-      tri_index(D, t, i, jj);
-      T yr = T(0), yi = T(0);
-      for (int k = 0; k < D; ++k) {
-        const T w = W[k];
-        const T air = Vr[i * LD + k], aii = Vi[i * LD + k];
-        const T ajr = Vr[jj * LD + k], aji = Vi[jj * LD + k];
-        yr += w * (air * ajr + aii * aji);
-        yi += w * (aii * ajr - air * aji);
+    if (dk) {
+      // Y = V M V^H with M = f(Lambda) + L o E (dk_stop): W = V M, then W V^H
+      dk_matrix_herm<T, D, LD, NT>(Ar, Ai, cs, tid);
+      for (int e = tid; e < D * D; e += NT) {
+        const int i = e / D, jj = e % D;
+        T xr = T(0), xi = T(0);
+        for (int k = 0; k < D; ++k) {
+          const T vr_ = Vr[i * LD + k], vi_ = Vi[i * LD + k];
+          const T mr = Ar[k * LD + jj], mi = Ai[k * LD + jj];
+          xr += vr_ * mr - vi_ * mi;
+          xi += vr_ * mi + vi_ * mr;
+        }
+        Wr[i * LD + jj] = xr;
+        Wi[i * LD + jj] = xi;
       }
-      Ar[i * LD + jj] = yr;
-      Ai[i * LD + jj] = yi;
-      Ar[jj * LD + i] = yr;
-      Ai[jj * LD + i] = -yi;
+      gsync<NT>();
+      for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+        int i, jj;
+        tri_index(D, t, i, jj);
+        T yr = T(0), yi = T(0);
+        for (int k = 0; k < D; ++k) {  // sum_k W_ik conj(V_jk)
+          const T wr_ = Wr[i * LD + k], wi_ = Wi[i * LD + k];
+          const T ajr = Vr[jj * LD + k], aji = Vi[jj * LD + k];
+          yr += wr_ * ajr + wi_ * aji;
+          yi += wi_ * ajr - wr_ * aji;
+        }
+        Ar[i * LD + jj] = yr;
+        Ai[i * LD + jj] = (i == jj) ? T(0) : yi;
+        Ar[jj * LD + i] = yr;
+        Ai[jj * LD + i] = (i == jj) ? T(0) : -yi;
+      }
+    } else {
+      for (int k = tid; k < D; k += NT) {
+        const T w = Ar[k * LD + k];
+        W[k] = w > T(0) ? w : T(0);
+      }
+      gsync<NT>();
+      // Y = V diag(max(w,0)) V^H, written back into (Ar, Ai)
+      for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+        int i, jj;
+        tri_index(D, t, i, jj);
+        T yr = T(0), yi = T(0);
+        for (int k = 0; k < D; ++k) {
+          const T w = W[k];
+          const T air = Vr[i * LD + k], aii = Vi[i * LD + k];
+          const T ajr = Vr[jj * LD + k], aji = Vi[jj * LD + k];
+          yr += w * (air * ajr + aii * aji);
+          yi += w * (aii * ajr - air * aji);
+        }
+        Ar[i * LD + jj] = yr;
+        Ai[i * LD + jj] = yi;
+        Ar[jj * LD + i] = yr;
+        Ai[jj * LD + i] = -yi;
+      }
     }
     gsync<NT>();
     // pack Y_k (and Y_{-k} = conj Y_k) back, scaled by 1/N

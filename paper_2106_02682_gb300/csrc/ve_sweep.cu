@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
     gsync<NT>();
     T* vs = reinterpret_cast<T*>(a.vstore) + p * D * D;
     int nsw = 0;
+    bool dk = false;  // the eigensolve stopped early: reconstruct with the first-order correction
     if (a.warm) {
       for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = vs[e];
       gsync<NT>();
@@ -193,29 +194,51 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
         A[j * LD + i] = acc;
       }
       gsync<NT>();
-      nsw = jacobi_sym<T, D, LD, NT, true, false>(A, V, cs, red, tid);
+      nsw = jacobi_sym<T, D, LD, NT, true, false, true>(A, V, cs, red, tid, &dk);
     } else {
-      nsw = jacobi_sym<T, D, LD, NT, true, true>(A, V, cs, red, tid);
+      nsw = jacobi_sym<T, D, LD, NT, true, true, true>(A, V, cs, red, tid, &dk);
     }
     if (a.stats && tid == 0) {
       atomicAdd(a.stats, (unsigned long long)nsw);
       atomicAdd(a.stats + 1, 1ull);
     }
     for (int e = tid; e < D * D; e += NT) vs[e] = V[(e / D) * LD + (e % D)];
-    for (int k = tid; k < D; k += NT) {
-      const T w = A[k * LD + k];
-      W[k] = w > T(0) ? w : T(0);
-    }
-    gsync<NT>();
-    // rho~ = V diag(max(w, 0)) V^T
-    for (int t = tid; t < D * (D + 1) / 2; t += NT) {
-      int i, j;
-      tri_index(D, t, i, j);
-      T s = T(0);
+    if (dk) {
+      // rho~ = V M V^T with M = f(Lambda) + L o E (dk_stop): Wt = V M, then Wt V^T
+      dk_matrix_sym<T, D, LD, NT>(A, cs, tid);
+      for (int e = tid; e < D * D; e += NT) {
+        const int i = e / D, j = e % D;
+        T acc = T(0);
 #pragma unroll 4
-      for (int k = 0; k < D; ++k) s += W[k] * V[i * LD + k] * V[j * LD + k];
-      A[i * LD + j] = s;
-      A[j * LD + i] = s;
+        for (int k = 0; k < D; ++k) acc += V[i * LD + k] * A[k * LD + j];
+        Wt[i * LD + j] = acc;
+      }
+      gsync<NT>();
+      for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+        int i, j;
+        tri_index(D, t, i, j);
+        T s = T(0);
+#pragma unroll 4
+        for (int k = 0; k < D; ++k) s += Wt[i * LD + k] * V[j * LD + k];
+        A[i * LD + j] = s;
+        A[j * LD + i] = s;
+      }
+    } else {
+      for (int k = tid; k < D; k += NT) {
+        const T w = A[k * LD + k];
+        W[k] = w > T(0) ? w : T(0);
+      }
+      gsync<NT>();
+      // rho~ = V diag(max(w, 0)) V^T
+      for (int t = tid; t < D * (D + 1) / 2; t += NT) {
+        int i, j;
+        tri_index(D, t, i, j);
+        T s = T(0);
+#pragma unroll 4
+        for (int k = 0; k < D; ++k) s += W[k] * V[i * LD + k] * V[j * LD + k];
+        A[i * LD + j] = s;
+        A[j * LD + i] = s;
+      }
     }
     gsync<NT>();
     T rr = T(0), en = T(0);
