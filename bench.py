@@ -342,14 +342,15 @@ def run_ours(args):
         # kernels of one sweep (the captured graph holds the same kernel nodes) x timed sweeps
         launches = int(round(sum(v[1] for v in prof.values()) / k_prof)) * args.steps
 
+        # ---- single-GPU extras (N = 1 only: they would hold the other GPUs idle)
         # ---- a batch of 64 paper-size instances against one-at-a-time handles
         batch = None
-        if not args.no_ttb and rank == 0:
+        if not args.no_ttb and world == 1:
             batch = batch_rate(ve, synth, "paper", 64, 200, ve.VE_PREC_FP64)
 
         # ---- time to a certified bound: plain float64 against the faster forms
         ttb = None
-        if not args.no_ttb and rank == 0:
+        if not args.no_ttb and world == 1:
             ttb = time_to_bound(args, ve, synth, stream)
 
         out = {
