@@ -132,9 +132,9 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload, precision):
-    """Per-launch DRAM traffic of `kernel` from the committed ncu summary, if it was taken on
-    the current sources; else None."""
+def ncu_record(kernel, workload, precision):
+    """The committed ncu record of `kernel` (DRAM traffic per launch, pipe utilisation), if it
+    was taken on the current sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
@@ -144,7 +144,7 @@ def ncu_traffic(kernel, workload, precision):
     rec = data.get(f"{workload}/{precision}/{kernel}")
     if not rec or rec.get("source_digest") != source_digest():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
 
 
 # ------------------------------------------------------------------ replica aggregation
@@ -334,7 +334,12 @@ def run_ours(args):
                     "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
         roof["kernel"] = dom
         roof["ms_per_launch"] = ms_launch
-        roof["traffic"] = ncu_traffic(dom, args.workload, args.precision)
+        rec = ncu_record(dom, args.workload, args.precision)
+        roof["traffic"] = rec.get("dram_bytes_per_launch") if rec else None
+        if rec and "pipe_busy_while_resident" in rec:
+            # the achieved fraction counts nominal flops only; the pipe counter shows how busy
+            # the unit the kernel is bound by actually is (ncu, same sources)
+            roof["ncu_pipe_busy"] = {"pipe": rec["pipe"], "frac": rec["pipe_busy_while_resident"]}
         roof["algorithmic_per_launch"] = wk
         stages = {s: {"ms_per_launch": prof[s][0] / max(1, prof[s][1]), "launches": prof[s][1],
                       "share": prof[s][0] / max(1e-12, sum(v[0] for v in prof.values()))}
