@@ -120,6 +120,10 @@ int ve_ham_xxz(int dim, double J, double delta, ve_hamiltonian* out);
  * N1, N2 <= 64; 2-D lattices with M_p <= 64.  With L = 4 the eigensolves stage their 256 x 256
  * matrices in a device workspace of ~3.2 MB per SM.
  * opt may be NULL (defaults).  On success *out owns all device memory until ve_destroy.
+ * The first sweep of each precision times the block DFT's launch shapes on the handle's data
+ * (results do not depend on the choice) and keeps the fastest; choices are cached per device,
+ * lattice, D and precision for the process, and in the text file named by the environment
+ * variable VE_TUNE_CACHE (read once, appended to) when it is set.
  * Errors: VE_EINVAL (bad shape, cluster does not tile the lattice, N < 2, bad options),
  * VE_EUNSUPPORTED (sizes outside the list above), VE_ENOMEM, VE_ECUDA. */
 int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_hamiltonian* ham,

@@ -185,6 +185,7 @@ struct ve_handle {
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
   bool fp64_phase = false;  // MIXED: switched to the float64-accurate phase
+  bool fft_tuned[2] = {false, false};  // DFT passes autotuned (float64, float32 spectrum)
   double mx_best = INFINITY;  // MIXED float32 phase: best residual and read-backs without a
   int mx_stall = 0;           // 1 % gain, kept across ve_iterate calls
   // per-stage profiling
@@ -270,6 +271,11 @@ cudaError_t issue_sweep(ve_handle* h, int arith, bool warm) {
   pa.gws = h->gws;
   const SmallArgs sa = small_args(h);
   cudaError_t e;
+  if (!warm && !h->fft_tuned[fp32 ? 1 : 0]) {
+    // a cold sweep runs uncaptured: time the DFT passes' launch shapes once (fft_tune)
+    if ((e = fft_tune(h->plan, h->X, h->specA, h->specB, h->tw, fp32, s)) != cudaSuccess) return e;
+    h->fft_tuned[fp32 ? 1 : 0] = true;
+  }
   auto mark = [&](int i) { return h->prof ? cudaEventRecord(h->ev[i], s) : cudaSuccess; };
   if ((e = mark(0)) != cudaSuccess) return e;
   if ((e = launch_pair(pa, arith, s)) != cudaSuccess) return e;

@@ -16,6 +16,12 @@
 // the partner map k -> -k.  A 2-D lattice takes one pass per axis.  Forward sign e^{-i}, no
 // scaling; the projection kernel applies 1/N.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "../../include/ve.h"
 #include "ve_device.cuh"
@@ -512,8 +518,11 @@ cudaError_t run_pass_t(const FftPlan& p, const FftPass& ps, int dir, const doubl
   const bool pow2 = (ps.n & (ps.n - 1)) == 0;
   // narrower entry chunks when the pass has few lines, so that the grid fills the GPU
   const long lines = (long)ps.A * ps.B;
-  int ec = FFT_EC;
-  while (ec > 8 && lines * ((p.E + ec - 1) / ec) < 304) ec /= 2;
+  int ec = ps.ec[sizeof(R) == 4 ? 1 : 0];
+  if (ec <= 0) {
+    ec = FFT_EC;
+    while (ec > 8 && lines * ((p.E + ec - 1) / ec) < 304) ec /= 2;
+  }
   const size_t smem = sizeof(V) * ps.n * ec * (pow2 ? 1 : 2);
   static unsigned long long mask = 0;
   cudaError_t e = smem_once(k_fft_pass<R>, 2 * sizeof(V) * 64 * FFT_EC, mask);
@@ -623,6 +632,145 @@ int fft_plan_build(FftPlan& p, int dim, const int M[2], int D) {
 cudaError_t launch_fft_tables(const FftPlan& p, double2* tw, cudaStream_t s) {
   k_fft_tables<<<(p.ntw + 255) / 256, 256, 0, s>>>(tw, p);
   return cudaGetLastError();
+}
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, std::string> g_tune;  // key -> "ec ec ec ec" (fwd0 fwd1 inv0 inv1)
+bool g_tune_loaded = false;
+
+std::string tune_key(const FftPlan& p, bool fp32) {
+  int dev = 0, sms = 0, ma = 0, mi = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, dev);
+  char k[128];
+  snprintf(k, sizeof(k), "cc%d%d_sm%d_dim%d_M%dx%d_D%d_%s", ma, mi, sms, p.dim, p.M0, p.M1, p.D,
+           fp32 ? "f32" : "f64");
+  return k;
+}
+
+void tune_load_file() {
+  g_tune_loaded = true;
+  const char* path = getenv("VE_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[128];
+  int a, b, c, d;
+  while (fscanf(f, "%127s %d %d %d %d", key, &a, &b, &c, &d) == 5) {
+    char v[64];
+    snprintf(v, sizeof(v), "%d %d %d %d", a, b, c, d);
+    g_tune[key] = v;
+  }
+  fclose(f);
+}
+
+void tune_store_file(const std::string& key, const std::string& val) {
+  const char* path = getenv("VE_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %s\n", key.c_str(), val.c_str());
+  fclose(f);
+}
+
+// Mean time of `reps` launches of one pass with entries-per-CTA ec (ms), or < 0 on error.
+float time_pass(const FftPlan& p, FftPass ps, int slot, int ec, int dir, const double* xin,
+                const void* cin, void* cout, double* xout, const double2* tw, bool fp32,
+                cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  ps.ec[slot] = ec;
+  const int reps = 5;
+  if (run_pass(p, ps, dir, xin, cin, cout, xout, tw, fp32, s) != cudaSuccess) return -1.f;
+  if (cudaEventRecord(e0, s) != cudaSuccess) return -1.f;
+  for (int r = 0; r < reps; ++r)
+    if (run_pass(p, ps, dir, xin, cin, cout, xout, tw, fp32, s) != cudaSuccess) return -1.f;
+  if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+    return -1.f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / reps;
+}
+
+}  // namespace
+
+cudaError_t fft_tune(FftPlan& p, const double* x, double2* bufA, double2* bufB, const double2* tw,
+                     bool fp32, cudaStream_t s) {
+  const int slot = fp32 ? 1 : 0;
+  const std::string key = tune_key(p, fp32);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_loaded) tune_load_file();
+    const auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      int v[4];
+      if (sscanf(it->second.c_str(), "%d %d %d %d", &v[0], &v[1], &v[2], &v[3]) == 4) {
+        p.fwd[0].ec[slot] = v[0];
+        p.fwd[1].ec[slot] = v[1];
+        p.inv[0].ec[slot] = v[2];
+        p.inv[1].ec[slot] = v[3];
+        return cudaSuccess;
+      }
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cudaGetLastError();
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cudaGetLastError();
+  }
+  // scratch block-row output for the last inverse pass: a spectrum buffer holds N D^2 doubles
+  double* xscratch = reinterpret_cast<double*>(bufA);
+  // the passes in use: forward then inverse (one each for a one-pass transform)
+  FftPass* passes[4] = {&p.fwd[0], &p.fwd[1], &p.inv[0], &p.inv[1]};
+  if (p.npass == 1) passes[1] = &p.inv[0];
+  const int n = p.npass == 1 ? 2 : 4;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < n && err == cudaSuccess; ++i) {
+    // (forward 0: x -> bufA; forward 1: bufA -> bufB; inverse 0: the spectrum -> the other
+    // buffer; inverse 1: that buffer -> scratch block row)
+    const bool fwd = p.npass == 1 ? i == 0 : i < 2;
+    const int k = p.npass == 1 ? 0 : (i % 2);
+    const double* xin = nullptr;
+    const void* cin = nullptr;
+    void* cout = nullptr;
+    double* xout = nullptr;
+    if (fwd && k == 0) { xin = x; cout = bufA; }
+    else if (fwd) { cin = bufA; cout = bufB; }
+    else if (p.npass == 1) { cin = bufB; xout = xscratch; }
+    else if (k == 0) { cin = bufA; cout = bufB; }
+    else { cin = bufB; xout = xscratch; }
+    int best = 0;
+    float best_ms = 0.f;
+    for (int ec = 8; ec <= FFT_EC; ec *= 2) {
+      const float ms = time_pass(p, *passes[i], slot, ec, fwd ? -1 : +1, xin, cin, cout, xout, tw,
+                                 fp32, s, e0, e1);
+      if (ms < 0.f) {
+        err = cudaGetLastError();
+        if (err == cudaSuccess) err = cudaErrorUnknown;
+        break;
+      }
+      if (best == 0 || ms < best_ms) {
+        best = ec;
+        best_ms = ms;
+      }
+    }
+    passes[i]->ec[slot] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return err;
+  char v[64];
+  snprintf(v, sizeof(v), "%d %d %d %d", p.fwd[0].ec[slot], p.fwd[1].ec[slot], p.inv[0].ec[slot],
+           p.inv[1].ec[slot]);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune.find(key) == g_tune.end()) {
+    g_tune[key] = v;
+    tune_store_file(key, v);
+  }
+  return cudaSuccess;
 }
 
 cudaError_t fft_forward(const FftPlan& p, const double* x, double2* bufA, double2* bufB,

@@ -106,6 +106,7 @@ struct FftPass {
   int twN;
   int w_off;    // offset of the length-n table exp(-2 pi i j / n) in the twiddle buffer
   int tw_off;   // offset of the length-twN table
+  int ec[2];    // entries per CTA chosen by fft_tune (float64, float32 passes); 0: heuristic
 };
 
 struct FftPlan {
@@ -123,6 +124,13 @@ cudaError_t launch_fft_tables(const FftPlan& p, double2* tw, cudaStream_t s);
 // fp32: the spectrum is float2 (the buffers are reinterpreted) and the passes run in float32.
 cudaError_t fft_forward(const FftPlan& p, const double* x, double2* bufA, double2* bufB,
                         const double2* tw, double2** spec, bool fp32, cudaStream_t s);
+// Autotuning of the passes' entries per CTA (8, 16 or 32; the result of a pass does not depend
+// on it): each candidate is timed on the caller's data -- x is only read, block-row outputs go to
+// bufA -- and the fastest kept in the plan.  Choices are cached per device, lattice, D and
+// precision for the process, and in the file named by VE_TUNE_CACHE when that is set.
+// Not to be called during stream capture.
+cudaError_t fft_tune(FftPlan& p, const double* x, double2* bufA, double2* bufB, const double2* tw,
+                     bool fp32, cudaStream_t s);
 // Inverse: spectrum (in `spec`, which is bufA or bufB) -> real first block row x.
 cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2* bufB, double* x,
                         const double2* tw, bool fp32, cudaStream_t s);

@@ -384,6 +384,32 @@ def test_state_roundtrip_resume_and_determinism(ve):
             ve.ve_destroy(x)
 
 
+def test_dft_tuning_is_cached_and_changes_no_result(ve, tmp_path, monkeypatch):
+    """The first sweep times the DFT passes' launch shapes once per shape and precision; the
+    choice goes to the VE_TUNE_CACHE file, is reused by a second handle, and the sweeps still
+    match the oracle."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("VE_TUNE_CACHE", str(path))
+    lattice, cluster = (2 * 91,), (2,)  # 91 clusters: a shape no other test uses
+    pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 0.9, 1)))
+    st = vo.initial_state(pb)
+    h1 = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 0.9))
+    h2 = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 0.9))
+    try:
+        ve.ve_iterate(h1, 5, 0.0)
+        lines = path.read_text().splitlines()
+        assert len(lines) == 1 and "M91x1_D16_f64" in lines[0], lines
+        ve.ve_iterate(h2, 5, 0.0)
+        assert path.read_text().splitlines() == lines
+        np.testing.assert_array_equal(ve.ve_get_state(h1), ve.ve_get_state(h2))
+        for _ in range(5):
+            vo.iterate(pb, st)
+        assert relerr(ve.ve_get_state(h1), vo.pack_state(pb, st)) < RTOL64
+    finally:
+        ve.ve_destroy(h1)
+        ve.ve_destroy(h2)
+
+
 def test_nonfinite_state_is_reported(ve):
     h = ve.ve_create((16,), (1,), ve.ve_ham_tfim(1, 1.0, 1.0))
     try:
