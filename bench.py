@@ -124,11 +124,17 @@ def stage_work(N, D, npass, ncanon):
 
 
 def source_digest():
+    """Digest of the kernel sources with comments and blank lines removed: it changes with the
+    code the ncu summaries were taken on, not with its comments."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_02682_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        code = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
+        h.update(f.encode())
+        h.update("\n".join(ln for ln in code if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

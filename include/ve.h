@@ -46,9 +46,10 @@ extern "C" {
 #define VE_PREC_MIXED 1 /* float32 arithmetic in the pair pass, the block DFT and both PSD
                            projections, float64 state and reductions; ve_iterate finishes in
                            VE_PREC_DF64 arithmetic                                         */
-#define VE_PREC_DF64 2  /* float64-accurate: the pair pass and both PSD projections in
-                           double-float words (two float32 numbers, ~2^-48 rounding) on the
-                           float32 pipe, everything else in float64                          */
+#define VE_PREC_DF64 2  /* the pair pass and both PSD projections in double-float words (an
+                           unevaluated sum of two float32 numbers: 48-bit significand, ~2^-48
+                           rounding against float64's 2^-53) on the float32 pipe, everything
+                           else in float64                                                    */
 
 #define VE_MAX_BONDS 4
 

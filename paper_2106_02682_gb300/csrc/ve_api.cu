@@ -184,7 +184,7 @@ struct ve_handle {
   DevStatus* hst = nullptr;  // pinned
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-  bool fp64_phase = false;  // MIXED: switched to the float64-accurate phase
+  bool fp64_phase = false;  // MIXED: switched to the double-float refinement phase
   bool fft_tuned[2] = {false, false};  // DFT passes autotuned (float64, float32 spectrum)
   double mx_best = INFINITY;  // MIXED float32 phase: best residual and read-backs without a
   int mx_stall = 0;           // 1 % gain, kept across ve_iterate calls

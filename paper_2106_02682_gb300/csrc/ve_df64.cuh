@@ -1,4 +1,4 @@
-// ve_df64.cuh -- float64-accurate arithmetic on the float32 pipe ("double-float").
+// ve_df64.cuh -- near-float64 arithmetic on the float32 pipe ("double-float").
 //
 // A df64 value is the unevaluated sum hi + lo of two float32 numbers with |lo| <= ulp(hi) / 2,
 // i.e. a 48-bit significand (relative rounding ~2^-48 = 3.6e-15) with the float32 exponent

@@ -7,7 +7,7 @@
 namespace ve {
 
 // Arithmetic of the per-matrix work (pair pass, projections): native float64, float32, or
-// float64-accurate double-float words on the float32 pipe (ve_df64.cuh).
+// double-float words (48-bit significand) on the float32 pipe (ve_df64.cuh).
 enum Arith { ARITH_FP64 = 0, ARITH_FP32 = 1, ARITH_DF64 = 2 };
 
 // Raise a kernel's dynamic shared-memory limit once per device (outside any stream capture:
