@@ -150,6 +150,11 @@ def full_hamiltonian_apply(lattice, onsite, bonds):
         for e, B in bonds:
             t = tuple((s[p] + e[p]) % lattice[p] for p in range(dim))
             terms.append((B, (index[s], index[t])))
+    return _apply_terms(terms, n), n
+
+
+def _apply_terms(terms, n):
+    """psi -> sum over (op, positions) of op acting on the spins `positions` of psi."""
 
     def apply(psi):
         psi = np.asarray(psi).reshape([2] * n)
@@ -165,7 +170,61 @@ def full_hamiltonian_apply(lattice, onsite, bonds):
             out += np.moveaxis(moved, list(range(k)), list(pos))
         return out.reshape(-1)
 
-    return apply, n
+    return apply
+
+
+def general_blocks(nspins, L, onsite, bonds):
+    """Cluster blocks of a general spin-1/2 Hamiltonian (Sec. 2.1 pairwise form, Sec. 2.3
+    cluster relaxation; no translation invariance), the input of Algorithm 5.
+
+    Spins 0 .. nspins-1 are grouped into N = nspins / L clusters of L consecutive spins
+    (cluster c holds spins c L .. c L + L - 1, in that factor order).  `onsite` is (nspins, 2, 2),
+    one single-spin term per spin; `bonds` is a list of (s, t, B), B a 4 x 4 operator on the
+    spins (s, t) with s the first factor.  A term inside one cluster goes to that cluster's
+    H_i; a term between clusters i < j goes to H_ij, cluster i the first factor.
+
+    Returns dict(Hi (N, m, m), Hij (K, D, D), pairs [(i, j)] for i < j in lexicographic order,
+    N, L, m, D)."""
+    assert nspins % L == 0 and nspins // L >= 2
+    N = nspins // L
+    m = 2 ** L
+    D = m * m
+    pairs = [(i, j) for i in range(N) for j in range(i + 1, N)]
+    index = {pq: p for p, pq in enumerate(pairs)}
+    Hi = np.zeros((N, m, m))
+    Hij = np.zeros((len(pairs), D, D))
+    for s in range(nspins):
+        Hi[s // L] += embed(np.asarray(onsite[s]), [s % L], L)
+    for s, t, B in bonds:
+        cs, ct = s // L, t // L
+        assert s != t
+        if cs == ct:
+            Hi[cs] += embed(np.asarray(B), [s % L, t % L], L)
+        elif cs < ct:
+            Hij[index[(cs, ct)]] += embed(np.asarray(B), [s % L, L + t % L], 2 * L)
+        else:
+            Hij[index[(ct, cs)]] += embed(np.asarray(B), [L + s % L, t % L], 2 * L)
+    return dict(Hi=Hi, Hij=Hij, pairs=pairs, N=N, L=L, m=m, D=D)
+
+
+def terms_apply(nspins, onsite, bonds):
+    """Matrix-free action of sum_s onsite[s] + sum_(s,t,B) B on 2^nspins amplitudes."""
+    terms = [(np.asarray(onsite[s]), (s,)) for s in range(nspins)]
+    terms += [(np.asarray(B), (s, t)) for s, t, B in bonds]
+    return _apply_terms(terms, nspins)
+
+
+def exact_ground_energy_terms(nspins, onsite, bonds):
+    """E_0 of a general spin Hamiltonian given as terms (as general_blocks), by exact
+    diagonalisation (dense up to 10 spins, Lanczos above)."""
+    apply = terms_apply(nspins, onsite, bonds)
+    dim = 2 ** nspins
+    if nspins <= 10:
+        H = np.stack([apply(col) for col in np.eye(dim)], axis=1)
+        return np.linalg.eigvalsh(H)[0]
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    op = LinearOperator((dim, dim), matvec=apply, dtype=np.float64)
+    return eigsh(op, k=1, which="SA", tol=1e-12, v0=np.ones(dim) / np.sqrt(dim))[0][0]
 
 
 def exact_ground_energy(lattice, onsite, bonds, return_state=False):

@@ -7,7 +7,9 @@ Only random-matrix and workload generators live here (no step of the solver's ar
   * circulant_first_row: a first block row X_{0,delta} obeying X_{0,-delta} = X_{0,delta}^T, the
     structure of the dual matrix in Algorithm 6;
   * workloads: the named benchmark instances (lattice, cluster, field) used by bench.py;
-  * batch_instances: seeded families of independent instances for batched runs.
+  * batch_instances: seeded families of independent instances for batched runs;
+  * disordered_chain: a general (not translation-invariant) spin chain as a list of terms, the
+    input of the general solver: random fields and long-range random couplings.
 The default seed is 20210604.
 """
 import numpy as np
@@ -120,3 +122,34 @@ def batch_instances(family="c4", count=256, seed=None):
         n = _supported_clusters(max(2, int(round(length / L))))
         out.append(dict(kind=kind, x=x, lattice=(n * L,), cluster=(L,)))
     return out
+
+
+_PX = np.array([[0.0, 1.0], [1.0, 0.0]])
+_PZ = np.array([[1.0, 0.0], [0.0, -1.0]])
+_PYPY = np.array([[0.0, 0.0, 0.0, -1.0], [0.0, 0.0, 1.0, 0.0], [0.0, 1.0, 0.0, 0.0],
+                  [-1.0, 0.0, 0.0, 0.0]])  # sigma^y (x) sigma^y, real
+
+
+def disordered_chain(nspins, kind="tfim", alpha=2.0, seed=None, field=(0.5, 1.5)):
+    """An open chain of `nspins` spin-1/2 with random fields and all-to-all couplings decaying as
+    1 / |s - t|^alpha, as terms: dict(onsite (nspins, 2, 2), bond_sites (nb, 2) int32 with s < t,
+    bond_ops (nb, 4, 4), spin s the first factor).
+
+    tfim: H = -sum_s h_s X_s - sum_{s<t} J_st Z_s Z_t,
+    xxz:  H = sum_{s<t} J_st (X_s X_t + Y_s Y_t + Delta_s Z_s Z_t) - sum_s h_s Z_s / 10,
+    with h_s ~ U[field], J_st = xi_st / |s - t|^alpha, xi_st ~ U[0.5, 1.5], Delta_s ~ U[0, 1.5]."""
+    rng = _rng(seed)
+    h = rng.uniform(field[0], field[1], size=nspins)
+    sites = np.array([(s, t) for s in range(nspins) for t in range(s + 1, nspins)],
+                     dtype=np.int32).reshape(-1, 2)
+    xi = rng.uniform(0.5, 1.5, size=len(sites))
+    J = xi / np.abs(sites[:, 1] - sites[:, 0]).astype(np.float64) ** alpha
+    if kind == "tfim":
+        onsite = -h[:, None, None] * _PX
+        ops = -J[:, None, None] * np.kron(_PZ, _PZ)
+    else:
+        delta = rng.uniform(0.0, 1.5, size=nspins)
+        onsite = -0.1 * h[:, None, None] * _PZ
+        ops = J[:, None, None] * (np.kron(_PX, _PX) + _PYPY
+                                  + delta[sites[:, 0], None, None] * np.kron(_PZ, _PZ))
+    return dict(nspins=nspins, onsite=onsite, bond_sites=sites, bond_ops=ops)
