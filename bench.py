@@ -123,13 +123,17 @@ def stage_work(N, D, npass, ncanon):
     }
 
 
-def source_digest():
-    """Digest of the kernel sources with comments and blank lines removed: it changes with the
-    code the ncu summaries were taken on, not with its comments."""
+# The translation units the Algorithm-6 kernels of the ncu records are compiled from.
+KERNEL_SOURCES = ("ve_bound.cu", "ve_df64.cuh", "ve_device.cuh", "ve_fft.cu", "ve_sweep.cu")
+
+
+def source_digest(files=KERNEL_SOURCES):
+    """Digest of kernel sources with comments and blank lines removed: it changes with the code
+    the ncu summaries were taken on, not with its comments."""
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_02682_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(files):
         with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
         code = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
