@@ -368,6 +368,12 @@ def run_ours(args):
         if not args.no_ttb and world == 1:
             ttb = time_to_bound(args, ve, synth, stream)
 
+        # ---- the general (not translation-invariant) solver on its 128-spin workload
+        general = None
+        if not args.no_ttb and world == 1:
+            general = general_rate(ve, synth, "lrtfim_N128_L1", 3, 10, stream, flush)
+            general["workload"] = "lrtfim_N128_L1"
+
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -377,7 +383,7 @@ def run_ours(args):
             "data": "synthetic (seeded spin Hamiltonian, no dataset)",
             "config": workload_config(args, N, D),
             "e2e": e2e, "gpu_launches": launches * world, "roofline": roof, "stages": stages,
-            "clocks": ck, "time_to_bound": ttb, "batch": batch,
+            "clocks": ck, "time_to_bound": ttb, "batch": batch, "general": general,
             "jacobi_sweeps_per_eigensolve": {"pair": jac_pair, "wavevector": jac_k},
             "last_status": {"iter": status.iter, "energy_per_spin": status.energy_per_spin,
                             "feas_err": status.feas_err},
@@ -655,10 +661,182 @@ def run_projection(args):
         flush=True)
 
 
+# ------------------------------------------------------------------ general (Algorithm 5)
+def general_oracle(name):
+    from oracle import alg5
+    from oracle import models as mo
+    from paper_2106_02682_gb300 import synth
+    terms, L = synth.general_terms(name)
+    bonds = [(int(s), int(t), B) for (s, t), B in zip(terms["bond_sites"], terms["bond_ops"])]
+    blocks = mo.general_blocks(terms["nspins"], L, terms["onsite"], bonds)
+    pb = alg5.GeneralProblem(blocks)
+    s5 = alg5.general_setup(blocks)
+    return alg5, pb, s5, alg5.initial_state(pb, s5)
+
+
+def general_oracle_rate(name, seconds):
+    alg5, pb, s5, st = general_oracle(name)
+    alg5.iterate(pb, s5, st)  # warm-up sweep
+    n, t0, c0 = 0, time.perf_counter(), time.process_time()
+    while True:
+        alg5.iterate(pb, s5, st)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return n / el, n, el, round((time.process_time() - c0) / el, 2)
+
+
+def general_rate(ve, synth, name, warmup, steps, stream, flush):
+    """Sweeps per second of the general solver on workload `name` (CUDA events on the handle's
+    stream around each ve_general_iterate(1), L2 flushed before each), then a profiled pass:
+    per-stage times, the X step's Jacobi sweeps, and the roofline of its round kernel."""
+    import torch
+    terms, L = synth.general_terms(name)
+    h = ve.ve_general_create(terms, L, ve.ve_default_options(stream=stream.cuda_stream))
+    try:
+        N, m, D, K = ve.ve_general_dims(h)
+        n = N * D
+        ve.ve_general_iterate(h, warmup)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a.record(stream)
+            ve.ve_general_iterate(h, 1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        k_prof = max(3, min(steps, 20))
+        ve.ve_general_profile(h, 1)
+        for _ in range(k_prof):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ve.ve_general_iterate(h, 1)
+        torch.cuda.synchronize()
+        pms, pl, jac = ve.ve_general_profile_read(h)
+        rms, rounds = ve.ve_general_profile_rounds(h)
+        ve.ve_general_profile(h, 0)
+        st = ve.ve_general_get_status(h)
+        cert = ve.ve_general_bound(h)
+    finally:
+        ve.ve_general_destroy(h)
+    total = sum(pms)
+    stages = {s: {"ms_per_sweep": pms[i] / k_prof, "launches_per_sweep": pl[i] / k_prof,
+                  "share": pms[i] / max(1e-12, total)} for i, s in enumerate(ve.GENERAL_STAGES)}
+    ms_round = rms / max(1, rounds)
+    flops_round = 10.0 * n * n
+    achieved = flops_round / (ms_round * 1e-3) / 1e12
+    xstep_ms = (pms[2] + pms[3]) / k_prof
+    return {
+        "value": steps / (ms * 1e-3), "ms_per_step": ms / steps, "nspins": terms["nspins"],
+        "clusters": N, "pair_dim": D, "pairs": K, "x_dim": n,
+        "launches_per_sweep": sum(pl) / k_prof, "stages": stages,
+        "jacobi_sweeps_per_x_step": jac,
+        "roofline": {"bound": "alu", "kernel": "k_dense_round", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal FP64 rate of the part (recipe table), not in "
+                                    "MEASURED_PEAKS.json",
+                     "ms_per_launch": ms_round, "traffic": None,
+                     "algorithmic_per_launch": {"flops": flops_round, "bytes": 64.0 * n * n,
+                                                "note": "10 n^2 flops; 8 n^2 words read+written, "
+                                                        "L2-resident"}},
+        "x_step_nominal_tflops": 13.0 / 3.0 * n ** 3 / (xstep_ms * 1e-3) / 1e12,
+        "last_status": {"iter": st.iter, "energy_per_spin": st.energy_per_spin,
+                        "feas_err": st.feas_err, "bound_per_spin": cert.bound_per_spin},
+    }
+
+
+def run_general(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02682_gb300 import synth, ve
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    steps, warmup = min(args.steps, 60), max(3, min(args.warmup, 10))
+    clocks = ClockSampler(0)
+    g = general_rate(ve, synth, args.workload, warmup, steps, stream, flush)
+    ck = clocks.stop()
+    # end to end through the public API with host buffers
+    terms, L = synth.general_terms(args.workload)
+    h = ve.ve_general_create(terms, L, ve.ve_default_options(stream=stream.cuda_stream))
+    try:
+        ve.ve_general_iterate(h, 3)
+        sb = ve.ve_general_state_size(h)
+        host = torch.empty(sb // 8, dtype=torch.float64, pin_memory=True).numpy()
+        ve.ve_general_get_state(h, host)
+        k_e2e = 10
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ve.ve_general_set_state(h, host)
+            ve.ve_general_iterate(h, 1)
+            ve.ve_general_get_state(h, host)
+        e2e_s = time.perf_counter() - t0
+    finally:
+        ve.ve_general_destroy(h)
+    rate, ns, el, cores = general_oracle_rate(args.workload, args.cpu_seconds)
+    w = synth.GENERAL_WORKLOADS[args.workload]
+    print(json.dumps({
+        "metric": "Algorithm 5 ADMM sweeps/s (general Hamiltonian, dense X step)", "value": g["value"],
+        "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": g["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded disordered long-range spin chain, no dataset)",
+        "config": {"workload": args.workload, **w, "clusters": g["clusters"], "pairs": g["pairs"],
+                   "pair_dim": g["pair_dim"], "x_dim": g["x_dim"], "mu": 10.0, "nu": 10.0,
+                   "eps": 2.0, "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas"},
+        "e2e": {"value": k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": sb,
+                "d2h_bytes_per_step": sb + 40,
+                "how": "per step: ve_general_set_state from pinned host, ve_general_iterate(1 sweep) "
+                       "with status read-back, ve_general_get_state to pinned host; wall clock"},
+        "gpu_launches": int(round(g["launches_per_sweep"] * steps)), "roofline": g["roofline"],
+        "stages": g["stages"], "jacobi_sweeps_per_x_step": g["jacobi_sweeps_per_x_step"],
+        "x_step_nominal_tflops": g["x_step_nominal_tflops"], "clocks": ck,
+        "last_status": g["last_status"],
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{ns} full sweeps of {args.workload} in {el:.1f} s "
+                                   "(numpy float64 oracle, Algorithm 5, one warm-up sweep)"},
+    }), flush=True)
+
+
+def run_general_reference(args):
+    alg5, pb, s5, st = general_oracle(args.workload)
+    for _ in range(args.warmup):
+        alg5.iterate(pb, s5, st)
+    t0, c0 = time.perf_counter(), time.process_time()
+    for _ in range(args.steps):
+        alg5.iterate(pb, s5, st)
+    el = time.perf_counter() - t0
+    cores = round((time.process_time() - c0) / el, 2)
+    value = args.steps / el
+    print(json.dumps({
+        "impl": "reference", "metric": "Algorithm 5 ADMM sweeps/s (general Hamiltonian, dense X step)",
+        "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full sweeps of {args.workload} after "
+                                   f"{args.warmup} warm-up sweeps (numpy float64 oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def main():
     args = parse()
+    general = args.workload.startswith(("lrtfim", "lrxxz"))
     if args.impl == "reference":
-        run_reference(args)
+        if general:
+            if dist_env()[1] == 0:
+                run_general_reference(args)
+        else:
+            run_reference(args)
+    elif general:
+        run_general(args)
     elif args.workload.startswith("batch_"):
         run_batch(args)
     elif args.workload in PROJ_WORKLOADS:

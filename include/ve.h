@@ -310,6 +310,90 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
 int ve_circulant_project_noalloc(const double* x_in, double* x_out, int dim, const int M[2], int D,
                                  int precision, void* stream);
 
+/* ---- general Hamiltonians: Algorithm 5 (Sec. 3.2, "practical scheme") -------------------
+ * No translation invariance: random fields, inhomogeneous or long-range couplings.  Every
+ * cluster i has its own H_i and rho_i, every pair i < j its own H_ij, rho~_ij, Lambda_ij,
+ * Lambda1_ij, Lambda2_ij, and X is one dense (N D) x (N D) matrix whose projection X <-
+ * Pi_{>=0}(X - eps G) runs as one eigensolve spread over the whole GPU (cyclic Jacobi in the
+ * circle ordering, one launch per round, warm-started from the previous sweep's eigenvectors).
+ * The X step takes the ascent sign X - eps G, as ve_create's solver does.
+ *
+ * The Hamiltonian is a list of terms on nspins spins:
+ *   H = sum_s onsite[s] + sum_b B_b acting on spins (bond_sites[2b], bond_sites[2b+1]),
+ * onsite[s]: 2x2 real symmetric (row-major, 4 doubles each; onsite NULL = none); B_b: 4x4 real
+ * symmetric (16 doubles each) with the first listed spin as its first tensor factor; spin basis
+ * (sigma^z = +1, sigma^z = -1).  Clusters are runs of cluster_spins consecutive spins: cluster c
+ * holds spins c L .. c L + L - 1 (L = cluster_spins, N = nspins / L clusters, m = 2^L, D = m^2).
+ * A term inside one cluster belongs to its H_i, a term between clusters i < j to H_ij (cluster i
+ * the first factor).  Pairs are numbered i < j in lexicographic order, K = N (N - 1) / 2. */
+typedef struct {
+  int nspins;
+  const double* onsite;
+  int nbond;
+  const int* bond_sites;
+  const double* bond_ops;
+} ve_terms;
+
+typedef struct ve_general ve_general;
+
+/* Build the cluster blocks (copied; the caller keeps the terms) and the initial state of Sec. 4
+ * (rho_i = I/m, rho~_ij = I/D, multipliers 0, X = I).  Supported: L in {1, 2, 3}, N >= 2,
+ * N D <= 1024, precision VE_PREC_FP64.  opt may be NULL (defaults of ve_default_options).
+ * Errors: VE_EINVAL (sizes, spins out of range, a bond on one spin, bad options),
+ * VE_EUNSUPPORTED (L > 3, N D > 1024, other precisions), VE_ENOMEM, VE_ECUDA. */
+int ve_general_create(const ve_terms* terms, int cluster_spins, const ve_options* opt,
+                      ve_general** out);
+void ve_general_destroy(ve_general* h);  /* NULL-safe */
+int ve_general_dims(const ve_general* h, int* N, int* m, int* D, long* K);
+
+/* Sweeps of Algorithm 5 until max_iter sweeps or, when tol > 0, until the residual is <= tol
+ * at a read-back (every check_every sweeps).  Convergence measures: energy per spin
+ * (sum_i Tr[H_i rho_i] + sum_{i<j} Tr[H_ij rho_ij]) / nspins with the closed-form pair
+ * marginals, Eq. (feasErr) as sqrt(sum_{i<j} (|A1 rho_ij - rho_i|^2 + |A2 rho_ij - rho_j|^2 +
+ * |rho_ij - rho~_ij|^2) / K), |energy change|, residual = max of the last two.  Synchronous
+ * (the X step's eigensolve reads its stopping test on the host once per Jacobi sweep).
+ * Returns as ve_iterate. */
+int ve_general_iterate(ve_general* h, long max_iter, double tol, ve_status* out);
+int ve_general_get_status(ve_general* h, ve_status* out);
+
+/* Certified lower bound of the current state (weak duality with the ADMM's own multipliers):
+ * raw_bound = sum_i lmin(K_i) + sum_{i<j} lmin(K_ij), K_ij = H'_ij + A1^* Lambda1_ij +
+ * A2^* Lambda2_ij, K_i = H'_i - sum_{j>i} Lambda1_ij - sum_{j<i} Lambda2_ji; x_min_eig =
+ * lmin(X); x_neg_correction = N m max(0, -x_min_eig); bound_per_spin = (raw_bound -
+ * x_neg_correction) / nspins.  All in float64 on the GPU.  Synchronous. */
+int ve_general_bound(ve_general* h, ve_cert* out);
+
+/* Packed state: rho_i (N m^2), rho~ (K D^2), Lambda (K D^2), Lambda1 (K m^2), Lambda2 (K m^2),
+ * X (N D x N D), float64, each block row-major; bytes must equal ve_general_state_size.
+ * ve_general_set_state clears the stored previous energy.  Eigenvectors of the last
+ * projections stay with the handle as the next eigensolves' start. */
+size_t ve_general_state_size(const ve_general* h);
+int ve_general_get_state(ve_general* h, double* host, size_t bytes);
+int ve_general_set_state(ve_general* h, const double* host, size_t bytes);
+
+/* Per-stage timing with CUDA events around every following sweep: 0 pair pass, 1 cluster
+ * marginals + Lambda1/Lambda2 + status, 2 dense eigensolve of the X step (W = Y V, Jacobi
+ * sweeps, Rayleigh quotients), 3 reconstruction X = V diag(max(lambda, 0)) V^T.
+ * ve_general_profile(h, 1) clears the accumulators; profile_read gives milliseconds and kernel
+ * launches per stage (arrays of VE_GENERAL_NSTAGE) and the mean Jacobi sweeps per X step. */
+#define VE_GENERAL_NSTAGE 4
+int ve_general_profile(ve_general* h, int enable);
+int ve_general_profile_read(ve_general* h, double* ms, long* launches, double* jacobi_sweeps);
+/* Device time of the profiled X-step Jacobi sweeps alone (CUDA events around each sweep's graph
+ * of n - 1 round launches and its convergence test) and the round launches they held. */
+int ve_general_profile_rounds(ve_general* h, double* ms, long* rounds);
+
+/* Pi_{>=0} of ONE real symmetric n x n matrix (device, row-major; used as (A + A^T)/2) by the
+ * whole-GPU eigensolver of the general solver's X step.  n even, 2 <= n <= 1024.  out may alias
+ * in.  workspace: device memory of ve_project_psd_dense_workspace_size(n) bytes (0 for an
+ * unsupported n), 256-byte aligned, owned by the caller; it keeps the eigenvectors, and
+ * warm = 1 starts from those left by the previous call on the same workspace and n (warm = 0
+ * starts from V = I).  *sweeps (may be NULL) receives the Jacobi sweeps taken.  Synchronises
+ * `stream` (once per Jacobi sweep).  Errors: VE_EINVAL (NULL, n, workspace), VE_ECUDA. */
+size_t ve_project_psd_dense_workspace_size(int n);
+int ve_project_psd_dense(const double* in, double* out, int n, int warm, void* workspace,
+                         size_t workspace_bytes, void* stream, int* sweeps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libve_gb300.so")
-SOURCES = ["ve_sweep.cu", "ve_fft.cu", "ve_bound.cu", "ve_api.cu", "ve_noalloc.cu", "ve_mlp.cu"]
+SOURCES = ["ve_sweep.cu", "ve_fft.cu", "ve_bound.cu", "ve_api.cu", "ve_noalloc.cu", "ve_mlp.cu",
+           "ve_dense.cu", "ve_general.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

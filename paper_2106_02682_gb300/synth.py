@@ -130,6 +130,22 @@ _PYPY = np.array([[0.0, 0.0, 0.0, -1.0], [0.0, 0.0, 1.0, 0.0], [0.0, 1.0, 0.0, 0
                   [-1.0, 0.0, 0.0, 0.0]])  # sigma^y (x) sigma^y, real
 
 
+# General (not translation-invariant) workloads: (spins, spins per cluster, model, alpha).
+GENERAL_WORKLOADS = {
+    # disordered TFI chain of 128 spins with all-to-all 1/r^2 couplings, single-spin clusters:
+    # 8128 pairs of 4 x 4 marginals, X of 512 x 512
+    "lrtfim_N128_L1": dict(nspins=128, L=1, kind="tfim", alpha=2.0),
+    # disordered XXZ chain of 64 spins, all-to-all 1/r^2, 2-spin clusters: 496 pairs of 16 x 16
+    # marginals, X of 512 x 512
+    "lrxxz_N64_L2": dict(nspins=64, L=2, kind="xxz", alpha=2.0),
+}
+
+
+def general_terms(name):
+    w = GENERAL_WORKLOADS[name]
+    return disordered_chain(w["nspins"], w["kind"], alpha=w["alpha"]), w["L"]
+
+
 def disordered_chain(nspins, kind="tfim", alpha=2.0, seed=None, field=(0.5, 1.5)):
     """An open chain of `nspins` spin-1/2 with random fields and all-to-all couplings decaying as
     1 / |s - t|^alpha, as terms: dict(onsite (nspins, 2, 2), bond_sites (nb, 2) int32 with s < t,

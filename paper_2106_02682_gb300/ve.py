@@ -28,6 +28,8 @@ VE_MAX_BONDS = 4
 VE_NSTAGE = 7
 VE_NOALLOC_SCRATCH_BYTES = (16 << 20) + (256 << 10)
 STAGES = ("pair", "rho0", "dual12", "status", "fft_forward", "xproj", "fft_inverse")
+VE_GENERAL_NSTAGE = 4
+GENERAL_STAGES = ("pair", "cluster", "dense_eig", "reconstruct")
 
 c_int, c_long, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_long, ctypes.c_double,
                                                ctypes.c_void_p, ctypes.c_size_t)
@@ -68,6 +70,11 @@ class ve_cert(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ve_terms(ctypes.Structure):
+    _fields_ = [("nspins", c_int), ("onsite", c_void_p), ("nbond", c_int),
+                ("bond_sites", c_void_p), ("bond_ops", c_void_p)]
 
 
 class VEError(RuntimeError):
@@ -131,6 +138,23 @@ def _load():
                                          c_int, c_void_p, c_size_t, c_void_p]),
         "ve_circulant_project_noalloc": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(c_int),
                                                  c_int, c_int, c_void_p]),
+        "ve_general_create": (c_int, [ctypes.POINTER(ve_terms), c_int, ctypes.POINTER(ve_options),
+                                      ctypes.POINTER(c_void_p)]),
+        "ve_general_destroy": (None, [c_void_p]),
+        "ve_general_dims": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                    ctypes.POINTER(c_int), ctypes.POINTER(c_long)]),
+        "ve_general_iterate": (c_int, [c_void_p, c_long, c_double, ctypes.POINTER(ve_status)]),
+        "ve_general_get_status": (c_int, [c_void_p, ctypes.POINTER(ve_status)]),
+        "ve_general_bound": (c_int, [c_void_p, ctypes.POINTER(ve_cert)]),
+        "ve_general_state_size": (c_size_t, [c_void_p]),
+        "ve_general_get_state": (c_int, [c_void_p, P_double, c_size_t]),
+        "ve_general_set_state": (c_int, [c_void_p, P_double, c_size_t]),
+        "ve_general_profile": (c_int, [c_void_p, c_int]),
+        "ve_general_profile_read": (c_int, [c_void_p, P_double, ctypes.POINTER(c_long), P_double]),
+        "ve_general_profile_rounds": (c_int, [c_void_p, P_double, ctypes.POINTER(c_long)]),
+        "ve_project_psd_dense_workspace_size": (c_size_t, [c_int]),
+        "ve_project_psd_dense": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_size_t,
+                                         c_void_p, ctypes.POINTER(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -424,3 +448,104 @@ def ve_mlp_predict(m, x, n_out):
     _check(_lib.ve_mlp_predict(c_void_p(m), xp, x.shape[0], y.ctypes.data_as(P_float)),
            "ve_mlp_predict")
     return y
+
+
+# ---- general Hamiltonians (Algorithm 5) ------------------------------------------------------
+def ve_general_create(terms, cluster_spins, opt=None):
+    """terms: dict(nspins, onsite (nspins, 2, 2) or None, bond_sites (nb, 2), bond_ops (nb, 4, 4)).
+    Returns a handle (int)."""
+    nspins = int(terms["nspins"])
+    onsite = terms.get("onsite")
+    on = None if onsite is None else np.ascontiguousarray(onsite, dtype=np.float64).reshape(nspins, 4)
+    sites = np.ascontiguousarray(terms["bond_sites"], dtype=np.int32).reshape(-1, 2)
+    ops = np.ascontiguousarray(terms["bond_ops"], dtype=np.float64).reshape(-1, 16)
+    t = ve_terms(nspins, on.ctypes.data if on is not None else None, sites.shape[0],
+                 sites.ctypes.data if sites.size else None, ops.ctypes.data if ops.size else None)
+    h = c_void_p()
+    _check(_lib.ve_general_create(ctypes.byref(t), int(cluster_spins),
+                                  ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)),
+           "ve_general_create")
+    return h.value
+
+
+def ve_general_destroy(h):
+    _lib.ve_general_destroy(c_void_p(h) if h else None)
+
+
+def ve_general_dims(h):
+    N, m, D, K = c_int(), c_int(), c_int(), c_long()
+    _check(_lib.ve_general_dims(c_void_p(h), ctypes.byref(N), ctypes.byref(m), ctypes.byref(D),
+                                ctypes.byref(K)), "ve_general_dims")
+    return N.value, m.value, D.value, K.value
+
+
+def ve_general_iterate(h, max_iter, tol=0.0):
+    st = ve_status()
+    code = _check(_lib.ve_general_iterate(c_void_p(h), int(max_iter), float(tol), ctypes.byref(st)),
+                  "ve_general_iterate")
+    return code, st
+
+
+def ve_general_get_status(h):
+    st = ve_status()
+    _check(_lib.ve_general_get_status(c_void_p(h), ctypes.byref(st)), "ve_general_get_status")
+    return st
+
+
+def ve_general_bound(h):
+    c = ve_cert()
+    _check(_lib.ve_general_bound(c_void_p(h), ctypes.byref(c)), "ve_general_bound")
+    return c
+
+
+def ve_general_state_size(h):
+    return _lib.ve_general_state_size(c_void_p(h))
+
+
+def ve_general_get_state(h, out=None):
+    n = ve_general_state_size(h)
+    if out is None:
+        out = np.empty(n // 8, dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.ve_general_get_state(c_void_p(h), out.ctypes.data_as(P_double), out.nbytes),
+           "ve_general_get_state")
+    return out
+
+
+def ve_general_set_state(h, vec):
+    vec = np.ascontiguousarray(vec, dtype=np.float64)
+    _check(_lib.ve_general_set_state(c_void_p(h), vec.ctypes.data_as(P_double), vec.nbytes),
+           "ve_general_set_state")
+
+
+def ve_general_profile(h, enable):
+    _check(_lib.ve_general_profile(c_void_p(h), int(enable)), "ve_general_profile")
+
+
+def ve_general_profile_read(h):
+    ms = (c_double * VE_GENERAL_NSTAGE)()
+    nl = (c_long * VE_GENERAL_NSTAGE)()
+    sw = c_double()
+    _check(_lib.ve_general_profile_read(c_void_p(h), ms, nl, ctypes.byref(sw)),
+           "ve_general_profile_read")
+    return list(ms), list(nl), sw.value
+
+
+def ve_general_profile_rounds(h):
+    ms, r = c_double(), c_long()
+    _check(_lib.ve_general_profile_rounds(c_void_p(h), ctypes.byref(ms), ctypes.byref(r)),
+           "ve_general_profile_rounds")
+    return ms.value, r.value
+
+
+def ve_project_psd_dense_workspace_size(n):
+    return _lib.ve_project_psd_dense_workspace_size(int(n))
+
+
+def ve_project_psd_dense(in_ptr, out_ptr, n, ws_ptr, ws_bytes, warm=0, stream=None):
+    """Returns the Jacobi sweeps taken."""
+    sw = c_int()
+    _check(_lib.ve_project_psd_dense(c_void_p(in_ptr), c_void_p(out_ptr), int(n), int(warm),
+                                     c_void_p(ws_ptr), int(ws_bytes), c_void_p(stream),
+                                     ctypes.byref(sw)), "ve_project_psd_dense")
+    return sw.value

@@ -44,7 +44,7 @@ def test_struct_layouts_match_the_header(ve, tmp_path):
     """Compile a C probe against include/ve.h and compare sizes/offsets with the ctypes mirror."""
     structs = {"ve_lattice": ve.ve_lattice, "ve_cluster": ve.ve_cluster,
                "ve_hamiltonian": ve.ve_hamiltonian, "ve_options": ve.ve_options,
-               "ve_status": ve.ve_status, "ve_cert": ve.ve_cert}
+               "ve_status": ve.ve_status, "ve_cert": ve.ve_cert, "ve_terms": ve.ve_terms}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ve.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
@@ -121,3 +121,44 @@ def test_null_handles_are_rejected(ve):
     ve.ve_destroy(None)
     assert ve.ve_circulant_workspace_size((3, 5), 16) > 0
     assert ve.ve_circulant_workspace_size((4 * 67,), 16) == 0
+
+
+def _terms(nspins, bonds=((0, 1),)):
+    sites = np.array(bonds, dtype=np.int32).reshape(-1, 2)
+    return dict(nspins=nspins, onsite=np.zeros((nspins, 2, 2)), bond_sites=sites,
+                bond_ops=np.zeros((len(sites), 4, 4)))
+
+
+@pytest.mark.parametrize("nspins,L,bonds,code", [
+    (8, 4, ((0, 1),), -5),         # 4-spin clusters: not built for the general solver
+    (7, 2, ((0, 1),), -1),         # clusters do not tile the spins
+    (2, 2, ((0, 1),), -1),         # a single cluster
+    (260, 1, ((0, 1),), -5),       # N D = 1040 > 1024: beyond the dense X step
+    (4, 1, ((2, 2),), -1),         # a bond on one spin
+    (4, 1, ((0, 4),), -1),         # a spin out of range
+])
+def test_general_create_rejects_bad_terms_before_touching_the_gpu(ve, nspins, L, bonds, code):
+    with pytest.raises(ve.VEError) as ei:
+        ve.ve_general_create(_terms(nspins, bonds), L)
+    assert ei.value.code == code
+
+
+def test_general_create_rejects_other_precisions_and_bad_options(ve):
+    for bad, code in ((dict(precision=ve.VE_PREC_MIXED), -5), (dict(mu=0.0), -1),
+                      (dict(check_every=0), -1)):
+        with pytest.raises(ve.VEError) as ei:
+            ve.ve_general_create(_terms(4), 1, ve.ve_default_options(**bad))
+        assert ei.value.code == code
+
+
+def test_general_null_handles_and_dense_workspace_sizes(ve):
+    assert ve.lib.ve_general_iterate(None, 1, 0.0, None) == -1
+    assert ve.lib.ve_general_bound(None, None) == -1
+    assert ve.lib.ve_general_state_size(None) == 0
+    assert ve.lib.ve_general_dims(None, None, None, None, None) == -1
+    ve.ve_general_destroy(None)
+    for n, ok in ((2, True), (24, True), (512, True), (1024, True), (511, False), (1026, False),
+                  (0, False)):
+        assert (ve.ve_project_psd_dense_workspace_size(n) > 0) == ok, n
+    # two n x n float64 matrices plus small vectors
+    assert ve.ve_project_psd_dense_workspace_size(512) >= 2 * 512 * 512 * 8
