@@ -717,7 +717,7 @@ def general_rate(ve, synth, name, warmup, steps, stream, flush):
             ve.ve_general_iterate(h, 1)
         torch.cuda.synchronize()
         pms, pl, jac = ve.ve_general_profile_read(h)
-        rms, rounds = ve.ve_general_profile_rounds(h)
+        rms, rounds, first_order = ve.ve_general_profile_rounds(h)
         ve.ve_general_profile(h, 0)
         st = ve.ve_general_get_status(h)
         cert = ve.ve_general_bound(h)
@@ -734,7 +734,7 @@ def general_rate(ve, synth, name, warmup, steps, stream, flush):
         "value": steps / (ms * 1e-3), "ms_per_step": ms / steps, "nspins": terms["nspins"],
         "clusters": N, "pair_dim": D, "pairs": K, "x_dim": n,
         "launches_per_sweep": sum(pl) / k_prof, "stages": stages,
-        "jacobi_sweeps_per_x_step": jac,
+        "jacobi_sweeps_per_x_step": jac, "x_steps_first_order": first_order / k_prof,
         "roofline": {"bound": "alu", "kernel": "k_dense_round", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "peak_source": "nominal FP64 rate of the part (recipe table), not in "
@@ -795,6 +795,7 @@ def run_general(args):
                        "with status read-back, ve_general_get_state to pinned host; wall clock"},
         "gpu_launches": int(round(g["launches_per_sweep"] * steps)), "roofline": g["roofline"],
         "stages": g["stages"], "jacobi_sweeps_per_x_step": g["jacobi_sweeps_per_x_step"],
+        "x_steps_first_order": g["x_steps_first_order"],
         "x_step_nominal_tflops": g["x_step_nominal_tflops"], "clocks": ck,
         "last_status": g["last_status"],
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

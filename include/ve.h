@@ -380,18 +380,28 @@ int ve_general_set_state(ve_general* h, const double* host, size_t bytes);
 int ve_general_profile(ve_general* h, int enable);
 int ve_general_profile_read(ve_general* h, double* ms, long* launches, double* jacobi_sweeps);
 /* Device time of the profiled X-step Jacobi sweeps alone (CUDA events around each sweep's graph
- * of n - 1 round launches and its convergence test) and the round launches they held. */
-int ve_general_profile_rounds(ve_general* h, double* ms, long* rounds);
+ * of n - 1 round launches and its convergence test), the round launches they held, and the X
+ * steps that ended with the first-order reconstruction (VE_DENSE_FIRST_ORDER below). */
+int ve_general_profile_rounds(ve_general* h, double* ms, long* rounds, long* first_order);
 
 /* Pi_{>=0} of ONE real symmetric n x n matrix (device, row-major; used as (A + A^T)/2) by the
  * whole-GPU eigensolver of the general solver's X step.  n even, 2 <= n <= 1024.  out may alias
  * in.  workspace: device memory of ve_project_psd_dense_workspace_size(n) bytes (0 for an
- * unsupported n), 256-byte aligned, owned by the caller; it keeps the eigenvectors, and
- * warm = 1 starts from those left by the previous call on the same workspace and n (warm = 0
- * starts from V = I).  *sweeps (may be NULL) receives the Jacobi sweeps taken.  Synchronises
- * `stream` (once per Jacobi sweep).  Errors: VE_EINVAL (NULL, n, workspace), VE_ECUDA. */
+ * unsupported n), 256-byte aligned, owned by the caller; it keeps the eigenvectors.
+ * flags: VE_DENSE_WARM starts from the eigenvectors left by the previous call on the same
+ * workspace and n (else from V = I).  VE_DENSE_FIRST_ORDER lets the sweeps stop early: once a
+ * sweep's rotations were small, A = V^T Y V is formed by one GEMM, and when its off-diagonal part
+ * E satisfies ||E||_F^4 <= (n u)^2 ||A||_F^2 d^2 and ||E||_F <= d/4 (d = distance of diag(A) from
+ * zero, u = 2^-53) the result is V (f(Lambda) + L o E) V^T, f = max(., 0), L the divided
+ * differences of f (Daleckii-Krein): as accurate as running the sweeps to the exact rule (the
+ * general solver's X step always does this).  Every Jacobi round is one launch over n/2 CTAs;
+ * the n - 1 rounds of a sweep are one CUDA graph.  *sweeps (may be NULL) receives the Jacobi
+ * sweeps taken, plus 1000 if the first-order reconstruction was used.  Synchronises `stream`
+ * (once per Jacobi sweep).  Errors: VE_EINVAL (NULL, n, workspace, flags), VE_ECUDA. */
+#define VE_DENSE_WARM 1
+#define VE_DENSE_FIRST_ORDER 2
 size_t ve_project_psd_dense_workspace_size(int n);
-int ve_project_psd_dense(const double* in, double* out, int n, int warm, void* workspace,
+int ve_project_psd_dense(const double* in, double* out, int n, int flags, void* workspace,
                          size_t workspace_bytes, void* stream, int* sweeps);
 
 #ifdef __cplusplus

@@ -20,7 +20,14 @@
 // Warm start: V from the previous call on the same workspace (consecutive ADMM sweeps project
 // nearby matrices), W = Y V by one GEMM.  Stopping: after a sweep whose rotated blocks satisfy
 // 2 sum a_pq^2 <= (n u)^2 ||Y||_F^2 (the rule of the batched eigensolvers).  Then
-// lambda_i = v_i.w_i and X = V diag(max(lambda, 0)) V^T by a GEMM.  The input is used as
+// lambda_i = v_i.w_i and X = V diag(max(lambda, 0)) V^T by a GEMM.
+// Early stop (allow_dk): once a sweep's rotations were small (2 sum a_pq^2 <= 1e-10 ||Y||_F^2,
+// so quadratic convergence has left A = V^T Y V within ~1e-10 of diagonal), A is formed by one
+// GEMM and its off-diagonal part E checked: ||E||_F^2 <= (n u)^2 ||A||_F^2 means converged
+// without the confirming sweep; ||E||_F^4 <= (n u)^2 ||A||_F^2 d^2 and ||E||_F <= d / 4, d the
+// distance of diag(A) from zero, means the first-order expansion f(A) = f(Lambda) + L o E
+// (Daleckii-Krein, f = max(., 0), L the divided differences) is as accurate as the exact rule,
+// and X = V (f(Lambda) + L o E) V^T by two GEMMs replaces the remaining sweeps.  The input is used as
 // (Y + Y^T) / 2: a_pq averages both orders and v_i.w_i = v_i^T Y v_i.
 #include <cstdint>
 
@@ -32,6 +39,8 @@ namespace ve {
 namespace {
 
 constexpr int RT = 128;  // threads of a round CTA
+// A sweep whose rotations summed below this fraction of ||Y||_F^2 triggers the explicit check.
+constexpr double kDkTrigger = 1e-10;
 
 template <int EPT>
 __global__ void __launch_bounds__(RT) k_dense_round(double* __restrict__ Vt, double* __restrict__ Wt,
@@ -60,20 +69,22 @@ __global__ void __launch_bounds__(RT) k_dense_round(double* __restrict__ Vt, dou
       s_qp = fma(xvq[e], xwp[e], s_qp);
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s_pp += __shfl_xor_sync(0xffffffffu, s_pp, o);
-    s_qq += __shfl_xor_sync(0xffffffffu, s_qq, o);
-    s_pq += __shfl_xor_sync(0xffffffffu, s_pq, o);
-    s_qp += __shfl_xor_sync(0xffffffffu, s_qp, o);
-  }
+  // Transposing butterfly: the four warp sums in 6 shuffles and 6 float64 adds a thread (not
+  // 20 of each).  Across 16 a lane keeps two of the values and hands over the other two, across
+  // 8 it keeps one, then three plain levels; lane L ends with the total of value
+  // 2 bit4(L) + bit3(L) of (s_pp, s_qq, s_pq, s_qp).
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    red[w][0] = s_pp;
-    red[w][1] = s_qq;
-    red[w][2] = s_pq;
-    red[w][3] = s_qp;
-  }
+  const bool hi = (lane & 16) != 0, mid = (lane & 8) != 0;
+  double k0 = hi ? s_pq : s_pp, k1 = hi ? s_qp : s_qq;
+  const double g0 = hi ? s_pp : s_pq, g1 = hi ? s_qq : s_qp;
+  k0 += __shfl_xor_sync(0xffffffffu, g0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, g1, 16);
+  double v = mid ? k1 : k0;
+  v += __shfl_xor_sync(0xffffffffu, mid ? k0 : k1, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  if ((lane & 7) == 0) red[w][lane >> 3] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double app = 0.0, aqq = 0.0, bpq = 0.0, bqp = 0.0;
@@ -123,6 +134,48 @@ __global__ void __launch_bounds__(256) k_dense_sweep_end(double* slot, int H, De
   }
 }
 
+// The explicit early-stop test on A = V^T Y V (B[i][j] = v_i.w_j, symmetrised).
+__global__ void __launch_bounds__(1024) k_dense_dk_check(const double* B, int n, DenseCtl* ctl) {
+  __shared__ double red[32];
+  double off = 0.0, d = INFINITY;
+  const size_t nn = (size_t)n * n;
+  for (size_t e = threadIdx.x; e < nn; e += 1024) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i < j) {
+      const double a = 0.5 * (B[e] + B[(size_t)j * n + i]);
+      off = fma(2.0 * a, a, off);
+    } else if (i == j) {
+      d = fmin(d, fabs(B[e]));
+    }
+  }
+  off = gsum<1024>(off, red);
+  d = gmin<1024>(d, red);
+  if (threadIdx.x == 0) {
+    const double tol = (double)n * JacobiTol<double>::u;
+    const double rel2 = tol * tol * ctl->nrm2;
+    int dk = 0;
+    if (off <= rel2) dk = 1;
+    else if (off * off <= rel2 * d * d && 16.0 * off <= d * d) dk = 2;
+    ctl->dk = dk;
+  }
+}
+
+// M = f(Lambda) + L o E from A (B, symmetrised) into M; lam receives the diagonal.
+__global__ void k_dense_dk_matrix(const double* B, double* M, double* lam, int n) {
+  const size_t nn = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const double li = B[(size_t)i * n + i];
+    if (i == j) {
+      M[e] = li > 0.0 ? li : 0.0;
+      lam[i] = li;
+    } else {
+      const double a = 0.5 * (B[e] + B[(size_t)j * n + i]);
+      M[e] = a * dk_weight<double>(li, B[(size_t)j * n + j]);
+    }
+  }
+}
+
 // ||Y||_F^2 (fixed order), and the control block reset for a new projection.
 __global__ void __launch_bounds__(1024) k_dense_begin(const double* Y, int n, double* slot, DenseCtl* ctl) {
   __shared__ double red[32];
@@ -136,6 +189,7 @@ __global__ void __launch_bounds__(1024) k_dense_begin(const double* Y, int n, do
     ctl->off2 = 0.0;
     ctl->converged = 0;
     ctl->sweeps = 0;
+    ctl->dk = 0;
   }
 }
 
@@ -268,7 +322,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t dense_ws_bytes(int n) {
   if (n < 2 || n > DENSE_MAX_N || (n & 1)) return 0;
   const size_t nn = (size_t)n * n * sizeof(double);
-  return 2 * al256(nn) + al256(n * sizeof(double)) + al256((n / 2) * sizeof(double)) +
+  return 3 * al256(nn) + al256(n * sizeof(double)) + al256((n / 2) * sizeof(double)) +
          al256(sizeof(DenseCtl));
 }
 
@@ -282,6 +336,8 @@ int dense_ws_init(DenseWs& w, int n, void* mem, size_t bytes) {
   w.Vt = (double*)p;
   p += al256(nn);
   w.Wt = (double*)p;
+  p += al256(nn);
+  w.Bt = (double*)p;
   p += al256(nn);
   w.lam = (double*)p;
   p += al256(n * sizeof(double));
@@ -338,6 +394,7 @@ cudaError_t sweep_graph(DenseWs& w, cudaStream_t s) {
 cudaError_t dense_eig(DenseWs& w, const double* Y, int mode, cudaStream_t s) {
   const int n = w.n;
   cudaError_t e;
+  w.dk_mode = 0;
   if (!w.hctl) {
     e = cudaMallocHost((void**)&w.hctl, sizeof(DenseCtl));
     if (e != cudaSuccess) return e;
@@ -379,6 +436,22 @@ cudaError_t dense_eig(DenseWs& w, const double* Y, int mode, cudaStream_t s) {
       ++sweeps;
       break;
     }
+    if (w.allow_dk && w.hctl->off2 <= kDkTrigger * w.hctl->nrm2) {
+      // A = V^T (Y V): B[i][j] = v_i.w_j
+      if ((e = gemm<false, true>(n, n, n, w.Vt, n, w.Wt, n, w.Bt, n, nullptr, s)) != cudaSuccess) return e;
+      k_dense_dk_check<<<1, 1024, 0, s>>>(w.Bt, n, w.ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      w.launches += 2;
+      if ((e = cudaMemcpyAsync(w.hctl, w.ctl, sizeof(DenseCtl), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      if (w.hctl->dk) {
+        w.dk_mode = w.hctl->dk;
+        ++w.dk_stops;
+        ++sweeps;
+        break;
+      }
+    }
   }
   w.last_sweeps = sweeps;
   w.total_sweeps += sweeps;
@@ -390,6 +463,15 @@ cudaError_t dense_eig(DenseWs& w, const double* Y, int mode, cudaStream_t s) {
 
 cudaError_t dense_reconstruct(DenseWs& w, double* X, cudaStream_t s) {
   const int n = w.n;
+  if (w.dk_mode == 2) {
+    // X = V M V^T = Vt^T (M Vt), M = f(Lambda) + L o E built in Wt (free after the check)
+    k_dense_dk_matrix<<<256, 256, 0, s>>>(w.Bt, w.Wt, w.lam, n);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = gemm<false, false>(n, n, n, w.Wt, n, w.Vt, n, w.Bt, n, nullptr, s);
+    if (e == cudaSuccess) e = gemm<true, false>(n, n, n, w.Vt, n, w.Bt, n, X, n, nullptr, s);
+    w.launches += 3;
+    return e;
+  }
   // X = V diag(max(lambda, 0)) V^T = Vt^T diag(.) Vt
   const cudaError_t e = gemm<true, false>(n, n, n, w.Vt, n, w.Vt, n, X, n, w.lam, s);
   w.launches += 1;

@@ -14,6 +14,8 @@ struct DenseCtl {
   double lmin;   // smallest lambda_i (dense_lmin)
   int converged; // the last sweep met the stopping rule
   int sweeps;    // sweeps of the current eigensolve
+  int dk;        // explicit check: 0 go on, 1 converged, 2 first-order reconstruction suffices
+  int pad;
 };
 
 // Device workspace of one n x n eigensolve (carved from caller memory by dense_ws_init); Vt
@@ -24,10 +26,14 @@ struct DenseWs {
   double* Wt = nullptr;     // n x n: row i = w_i = Y v_i
   double* lam = nullptr;    // n: lambda_i = v_i.w_i after dense_eig
   double* slot = nullptr;   // n/2: per-CTA sum of a_pq^2 over a sweep
+  double* Bt = nullptr;     // n x n: A = V^T Y V formed explicitly for the early-stop check
   DenseCtl* ctl = nullptr;  // device
   DenseCtl* hctl = nullptr; // pinned host copy (allocated on first use)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  bool allow_dk = false;    // take the first-order (Daleckii-Krein) early stop
+  int dk_mode = 0;          // how the last eigensolve stopped (DenseCtl::dk)
+  long dk_stops = 0;        // eigensolves ended by the explicit check
   int last_sweeps = 0;
   long total_sweeps = 0;
   long launches = 0;        // kernels launched (graph rounds counted one by one)
@@ -50,7 +56,8 @@ void dense_ws_release(DenseWs& w);
 // V = I, DENSE_WARM from the Vt left by the previous call.  Synchronises `s` once per sweep (the
 // stopping test is read on the host).  Not to be called during stream capture.
 cudaError_t dense_eig(DenseWs& w, const double* Y, int mode, cudaStream_t s);
-// X = V diag(max(lambda, 0)) V^T after dense_eig (X may alias the Y given to it).
+// X = V diag(max(lambda, 0)) V^T after dense_eig, or V (f(Lambda) + L o E) V^T when the
+// eigensolve took the first-order stop (X may alias the Y given to dense_eig).
 cudaError_t dense_reconstruct(DenseWs& w, double* X, cudaStream_t s);
 // ctl->lmin = min_i lambda_i after dense_eig.
 cudaError_t dense_lmin(DenseWs& w, cudaStream_t s);

@@ -576,7 +576,7 @@ struct ve_general {
   cudaEvent_t ev[VE_GENERAL_NSTAGE + 1] = {};
   double prof_ms[VE_GENERAL_NSTAGE] = {};
   long prof_launch[VE_GENERAL_NSTAGE] = {};
-  long prof_sweeps = 0, prof_solves = 0;
+  long prof_sweeps = 0, prof_solves = 0, prof_dk = 0;
 };
 
 namespace {
@@ -671,6 +671,7 @@ int sweep(ve_general* h) {
     h->prof_launch[3] += 1;
     h->prof_sweeps += h->dws.last_sweeps;
     h->prof_solves += 1;
+    h->prof_dk += h->dws.dk_mode == 2 ? 1 : 0;
   }
   return VE_OK;
 }
@@ -823,6 +824,8 @@ int ve_general_create(const ve_terms* t, int cluster_spins, const ve_options* op
   int rc = VE_OK;
   if (dense_ws_init(h->dws, (int)n, dmem, dense) != 0 || dense_ws_init(h->bws, (int)n, bmem, dense) != 0)
     rc = VE_EINVAL;
+  // the X step may end with the first-order correction; the bound's eigensolve of X stays exact
+  h->dws.allow_dk = true;
   if (rc == VE_OK) {
     if (o.stream) {
       h->stream = (cudaStream_t)o.stream;
@@ -985,7 +988,7 @@ int ve_general_profile(ve_general* h, int enable) {
     h->prof_ms[k] = 0.0;
     h->prof_launch[k] = 0;
   }
-  h->prof_sweeps = h->prof_solves = 0;
+  h->prof_sweeps = h->prof_solves = h->prof_dk = 0;
   return VE_OK;
 }
 
@@ -999,26 +1002,29 @@ int ve_general_profile_read(ve_general* h, double* ms, long* launches, double* j
   return VE_OK;
 }
 
-int ve_general_profile_rounds(ve_general* h, double* ms, long* rounds) {
+int ve_general_profile_rounds(ve_general* h, double* ms, long* rounds, long* first_order) {
   if (!h) return VE_EINVAL;
   if (ms) *ms = h->dws.graph_ms;
   if (rounds) *rounds = h->dws.graph_rounds;
+  if (first_order) *first_order = h->prof_dk;
   return VE_OK;
 }
 
 // ---- standalone dense projection
 size_t ve_project_psd_dense_workspace_size(int n) { return dense_ws_bytes(n); }
 
-int ve_project_psd_dense(const double* in, double* out, int n, int warm, void* workspace,
+int ve_project_psd_dense(const double* in, double* out, int n, int flags, void* workspace,
                          size_t workspace_bytes, void* stream, int* sweeps) {
-  if (!in || !out || dense_ws_bytes(n) == 0) return VE_EINVAL;
+  if (!in || !out || dense_ws_bytes(n) == 0 || (flags & ~(VE_DENSE_WARM | VE_DENSE_FIRST_ORDER)))
+    return VE_EINVAL;
   DenseWs w;
   if (dense_ws_init(w, n, workspace, workspace_bytes) != 0) return VE_EINVAL;
+  w.allow_dk = (flags & VE_DENSE_FIRST_ORDER) != 0;
   const cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = dense_eig(w, in, warm ? DENSE_WARM : DENSE_COLD, s);
+  cudaError_t e = dense_eig(w, in, (flags & VE_DENSE_WARM) ? DENSE_WARM : DENSE_COLD, s);
   if (e == cudaSuccess) e = dense_reconstruct(w, out, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (sweeps) *sweeps = w.last_sweeps;
+  if (sweeps) *sweeps = w.last_sweeps + (w.dk_mode == 2 ? 1000 : 0);
   dense_ws_release(w);
   return e == cudaSuccess ? VE_OK : VE_ECUDA;
 }

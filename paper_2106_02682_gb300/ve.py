@@ -151,7 +151,8 @@ def _load():
         "ve_general_set_state": (c_int, [c_void_p, P_double, c_size_t]),
         "ve_general_profile": (c_int, [c_void_p, c_int]),
         "ve_general_profile_read": (c_int, [c_void_p, P_double, ctypes.POINTER(c_long), P_double]),
-        "ve_general_profile_rounds": (c_int, [c_void_p, P_double, ctypes.POINTER(c_long)]),
+        "ve_general_profile_rounds": (c_int, [c_void_p, P_double, ctypes.POINTER(c_long),
+                                              ctypes.POINTER(c_long)]),
         "ve_project_psd_dense_workspace_size": (c_size_t, [c_int]),
         "ve_project_psd_dense": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_size_t,
                                          c_void_p, ctypes.POINTER(c_int)]),
@@ -532,20 +533,27 @@ def ve_general_profile_read(h):
 
 
 def ve_general_profile_rounds(h):
-    ms, r = c_double(), c_long()
-    _check(_lib.ve_general_profile_rounds(c_void_p(h), ctypes.byref(ms), ctypes.byref(r)),
-           "ve_general_profile_rounds")
-    return ms.value, r.value
+    """(ms of the profiled Jacobi sweeps, round launches in them, X steps ended first-order)."""
+    ms, r, fo = c_double(), c_long(), c_long()
+    _check(_lib.ve_general_profile_rounds(c_void_p(h), ctypes.byref(ms), ctypes.byref(r),
+                                          ctypes.byref(fo)), "ve_general_profile_rounds")
+    return ms.value, r.value, fo.value
 
 
 def ve_project_psd_dense_workspace_size(n):
     return _lib.ve_project_psd_dense_workspace_size(int(n))
 
 
-def ve_project_psd_dense(in_ptr, out_ptr, n, ws_ptr, ws_bytes, warm=0, stream=None):
-    """Returns the Jacobi sweeps taken."""
+VE_DENSE_WARM = 1
+VE_DENSE_FIRST_ORDER = 2
+
+
+def ve_project_psd_dense(in_ptr, out_ptr, n, ws_ptr, ws_bytes, warm=0, stream=None,
+                         first_order=False):
+    """Returns the Jacobi sweeps taken (+1000 when the first-order reconstruction ended them)."""
     sw = c_int()
-    _check(_lib.ve_project_psd_dense(c_void_p(in_ptr), c_void_p(out_ptr), int(n), int(warm),
+    flags = (VE_DENSE_WARM if warm else 0) | (VE_DENSE_FIRST_ORDER if first_order else 0)
+    _check(_lib.ve_project_psd_dense(c_void_p(in_ptr), c_void_p(out_ptr), int(n), flags,
                                      c_void_p(ws_ptr), int(ws_bytes), c_void_p(stream),
                                      ctypes.byref(sw)), "ve_project_psd_dense")
     return sw.value

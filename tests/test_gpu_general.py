@@ -40,14 +40,15 @@ def relerr(a, b):
 
 
 # ------------------------------------------------------------------ dense projection
-def _dense(ve, Y, ws=None, warm=0, alias=False):
+def _dense(ve, Y, ws=None, warm=0, alias=False, first_order=False):
     n = Y.shape[0]
     nb = ve.ve_project_psd_dense_workspace_size(n)
     if ws is None:
         ws = torch.empty(nb // 8 + 32, dtype=torch.float64, device="cuda")
     yin = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
     out = yin if alias else torch.empty_like(yin)
-    sweeps = ve.ve_project_psd_dense(yin.data_ptr(), out.data_ptr(), n, ws.data_ptr(), nb, warm)
+    sweeps = ve.ve_project_psd_dense(yin.data_ptr(), out.data_ptr(), n, ws.data_ptr(), nb, warm,
+                                     first_order=first_order)
     return out.cpu().numpy(), sweeps, ws
 
 
@@ -59,6 +60,16 @@ def test_dense_projection_matches_the_oracle(ve, n):
         ref = proj_psd(Y)
         assert relerr(X, ref) < tol(n), (n, relerr(X, ref))
         assert 1 <= sweeps <= 24
+
+
+@pytest.mark.parametrize("n", [64, 512])
+def test_dense_projection_is_reproducible(ve, n):
+    # fixed-order reductions throughout: the same input gives the same bits
+    Y = synth.symmetric_batch(2, n, seed=7 + n)[1]
+    Xa, sa, _ = _dense(ve, Y)
+    Xb, sb, _ = _dense(ve, Y)
+    assert sa == sb
+    np.testing.assert_array_equal(Xa, Xb)
 
 
 def test_dense_projection_warm_restart_and_aliasing(ve):
@@ -76,6 +87,28 @@ def test_dense_projection_warm_restart_and_aliasing(ve):
     X2, s2, _ = _dense(ve, Y2, ws=ws, warm=1, alias=True)
     assert relerr(X2, proj_psd(Y2)) < tol(n)
     assert s2 < s0
+
+
+@pytest.mark.parametrize("n", [64, 256, 512])
+def test_dense_first_order_stop_is_as_accurate_as_the_sweeps(ve, n):
+    # from the eigenvectors of Y, a nearby matrix: the explicit check on A = V^T Y' V ends the
+    # sweeps early, with the Daleckii-Krein reconstruction when the spectrum keeps away from 0
+    rng = np.random.default_rng(n)
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    lam = rng.uniform(0.05, 1.0, size=n) * rng.choice([-1.0, 1.0], size=n)
+    Y = (Q * lam) @ Q.T
+    _, _, ws = _dense(ve, Y)
+    saved = ws.clone()
+    E = rng.normal(size=(n, n)) * 1e-4
+    Y2 = Y + 0.5 * (E + E.T)
+    ref = proj_psd(Y2)
+    Xe, se, _ = _dense(ve, Y2, ws=ws, warm=1)
+    Xd, sd, _ = _dense(ve, Y2, ws=saved, warm=1, first_order=True)
+    assert relerr(Xe, ref) < tol(n)
+    assert relerr(Xd, ref) < tol(n)
+    assert sd % 1000 < se                 # the explicit check saved sweeps
+    if n == 256:
+        assert sd >= 1000                  # ... and here ended with the first-order reconstruction
 
 
 def test_dense_projection_of_psd_and_nsd_matrices(ve):
