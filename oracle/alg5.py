@@ -20,13 +20,32 @@ from .ve_oracle import (A1, A1_adj, A2, A2_adj, G_00, G_pair, T_inverse, eff_ham
 
 
 class GeneralProblem:
-    """An Algorithm-5 instance from cluster blocks (models.general_blocks): N clusters of L
-    spins, H_i (N, m, m), H_ij (K, D, D) for the pairs i < j in lexicographic order."""
+    """An Algorithm-5 instance from cluster blocks (models.general_blocks, or
+    fermions.fermion_blocks): N clusters of L sites, H_i (N, m, m), H_ij (K, D, D) for the pairs
+    i < j in lexicographic order.  fermionic=True takes the global matrix of Eq. (sdpFerm):
+    its off-diagonal blocks carry the parity signs of fermions.parity_signs (the diagonal blocks
+    and the partial traces are the spin ones)."""
 
-    def __init__(self, blocks, mu=10.0, nu=10.0, eps=2.0):
+    def __init__(self, blocks, mu=10.0, nu=10.0, eps=2.0, fermionic=False):
         self.N, self.L, self.m, self.D = blocks['N'], blocks['L'], blocks['m'], blocks['D']
         self.mu, self.nu, self.eps = float(mu), float(nu), float(eps)
+        self.sign = None
+        if fermionic:
+            from .fermions import parity_signs
+            self.sign = parity_signs(self.m)
         assert self.N >= 2
+
+
+def _G_pair(pb, rho):
+    """Off-diagonal blocks of the global matrix (with the fermionic parity signs if any)."""
+    g = G_pair(rho)
+    return g if pb.sign is None else pb.sign * g
+
+
+def _eff_ham_pair(pb, H, Xij):
+    """H'_ij of Eq. (effHam): H minus the adjoint of the off-diagonal G map applied to X_ij (and
+    its transpose); the signed map's adjoint applies the same signs to X first."""
+    return eff_ham_pair(H, Xij if pb.sign is None else pb.sign * Xij)
 
 
 def general_setup(blocks):
@@ -83,7 +102,7 @@ def iterate(pb, s5, st):
     X = st['X']
     # effective Hamiltonians, Eq. (effHam)
     Hp_i = [eff_ham_0(s5['Hi'][i], X[i * D:(i + 1) * D, i * D:(i + 1) * D]) for i in range(N)]
-    Hp_ij = eff_ham_pair(s5['Hij'], pair_blocks(X, N, D, pi, pj))
+    Hp_ij = _eff_ham_pair(pb, s5['Hij'], pair_blocks(X, N, D, pi, pj))
     # closed-form pair update, Eq. (rhoijUpdate)
     rho_i = st['rho']
     rhs = (mu * st['rt'] + A1_adj(nu * rho_i[pi] - st['lam1'])
@@ -105,7 +124,7 @@ def iterate(pb, s5, st):
     lam2 = st['lam2'] + nu * (a2 - new_rho_i[pj])
     # global matrix G[{rho_i}, {rho_ij}] (Sec. 2.2) and the X step
     G4 = np.zeros((N, N, D, D))
-    g = G_pair(rho)
+    g = _G_pair(pb, rho)
     G4[pi, pj] = g
     G4[pj, pi] = np.swapaxes(g, 1, 2)
     for i in range(N):
@@ -147,7 +166,7 @@ def certified_bound(pb, s5, st):
     N, m, D, L = pb.N, pb.m, pb.D, pb.L
     pi, pj = _pair_index(s5)
     X = st['X']
-    Kp = (eff_ham_pair(s5['Hij'], pair_blocks(X, N, D, pi, pj)) + A1_adj(st['lam1'])
+    Kp = (_eff_ham_pair(pb, s5['Hij'], pair_blocks(X, N, D, pi, pj)) + A1_adj(st['lam1'])
           + A2_adj(st['lam2']))
     Ki = np.array([eff_ham_0(s5['Hi'][i], X[i * D:(i + 1) * D, i * D:(i + 1) * D])
                    for i in range(N)])
