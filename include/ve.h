@@ -334,6 +334,29 @@ typedef struct {
   const double* bond_ops;
 } ve_terms;
 
+/* Spinless fermions (the paper's fermionic section, Eq. (spinlessFerm) and its long-range form):
+ *   H = sum_k hop_t[k] (a_i^dagger a_j + a_j^dagger a_i), (i, j) = hop_sites[2k], hop_sites[2k+1]
+ *     + sum_k pair_v[k] (n_i - 1/2)(n_j - 1/2),         (i, j) = pair_sites[2k], pair_sites[2k+1]
+ * on nsites sites (i != j in every term).  Clusters are runs of cluster_sites consecutive sites,
+ * as for spins.  ve_general_create_fermions builds the blocks of Eq. (sdpFerm): each cluster's
+ * terms under the Jordan-Wigner transformation in the cluster's site order, each pair's terms
+ * under the one in the pair's order (the first cluster's sites first); a site's basis is
+ * (empty, occupied), a^dagger acting as [[0, 0], [1, 0]] after a sigma^z string over the earlier
+ * sites.  The global matrix then carries parity signs on its off-diagonal blocks: with the
+ * complete collection of matrix units, entry (a, b), (c, d) of G_ij is multiplied by
+ * (-1)^(p(a) (p(c) + p(d))), p the parity of a cluster state's occupation bits (an operator of
+ * the second cluster that changes the parity carries the first cluster's parity string), and
+ * H'_ij takes the adjoint of that signed map.  Everything else is ve_general's solver. */
+typedef struct {
+  int nsites;
+  int nhop;
+  const int* hop_sites;
+  const double* hop_t;
+  int npair;
+  const int* pair_sites;
+  const double* pair_v;
+} ve_fermion_terms;
+
 typedef struct ve_general ve_general;
 
 /* Build the cluster blocks (copied; the caller keeps the terms) and the initial state of Sec. 4
@@ -343,6 +366,15 @@ typedef struct ve_general ve_general;
  * VE_EUNSUPPORTED (L > 3, N D > 1024, other precisions), VE_ENOMEM, VE_ECUDA. */
 int ve_general_create(const ve_terms* terms, int cluster_spins, const ve_options* opt,
                       ve_general** out);
+/* The same for spinless fermions (sizes and errors as ve_general_create, with sites for spins);
+ * every other ve_general_* call applies to the handle unchanged. */
+int ve_general_create_fermions(const ve_fermion_terms* terms, int cluster_sites,
+                               const ve_options* opt, ve_general** out);
+/* The cluster blocks those two calls build, written to host memory without touching a GPU:
+ * Hi (N m^2) and Hij (K D^2, pairs i < j in lexicographic order), row-major.  Errors as for
+ * the create calls (the options are not checked). */
+int ve_spin_blocks(const ve_terms* terms, int cluster_spins, double* Hi, double* Hij);
+int ve_fermion_blocks(const ve_fermion_terms* terms, int cluster_sites, double* Hi, double* Hij);
 void ve_general_destroy(ve_general* h);  /* NULL-safe */
 int ve_general_dims(const ve_general* h, int* N, int* m, int* D, long* K);
 

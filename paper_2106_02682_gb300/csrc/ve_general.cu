@@ -58,8 +58,17 @@ struct GenArgs {
   double* parti;        // N: Tr[H_i rho_i]
   double* vstore;       // K D^2: eigenvectors of the last pair projections
   int warm;
+  int fermionic;        // parity signs on the off-diagonal blocks of G and in H' (Eq. (sdpFerm))
   GenStatus* st;
 };
+
+// Parity sign of entry (a, b), (c, d) of an off-diagonal block of the fermionic global matrix:
+// in the pair's Jordan-Wigner ordering a second-cluster operator E_cd that changes the fermion
+// parity carries the first cluster's parity string P, and E_ab^dagger P = (-1)^p(a) E_ba; so the
+// sign is odd when p(a) (p(c) + p(d)) is odd, p the parity of a cluster basis state's bits.
+__device__ __forceinline__ bool parity_odd(int a, int c, int d) {
+  return ((__popc(a) & (__popc(c) ^ __popc(d))) & 1) != 0;
+}
 
 // Index of the pair (i, j), i < j, in lexicographic order.
 __host__ __device__ __forceinline__ long pair_index(int N, int i, int j) {
@@ -123,8 +132,14 @@ __global__ void __launch_bounds__(GroupShape<D>::NT, GroupShape<D>::MINB) k5_pai
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
       const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
-      // (R^* X)_{(a,b),(c,d)} = X_{(a,c),(d,b)} and its transpose X_{(c,a),(b,d)}
-      const T hp = Hb[e] - Xs[(pa * m + pc) * D + (pd * m + pb)] - Xs[(pc * m + pa) * D + (pb * m + pd)];
+      // (R^* X)_{(a,b),(c,d)} = X_{(a,c),(d,b)} and its transpose X_{(c,a),(b,d)} (with the
+      // parity signs of those X entries for fermions)
+      T x1 = Xs[(pa * m + pc) * D + (pd * m + pb)], x2 = Xs[(pc * m + pa) * D + (pb * m + pd)];
+      if (a.fermionic) {
+        if (parity_odd(pa, pd, pb)) x1 = -x1;
+        if (parity_odd(pc, pb, pd)) x2 = -x2;
+      }
+      const T hp = Hb[e] - x1 - x2;
       T y = mu * rt[e] + lam[e] - hp;
       if (pb == pd) y += nu * rhoi[pa * m + pc] - l1[pa * m + pc];
       if (pa == pc) y += nu * rhoj[pb * m + pd] - l2[pb * m + pd];
@@ -243,8 +258,11 @@ __global__ void __launch_bounds__(GroupShape<D>::NT, GroupShape<D>::MINB) k5_pai
       const T rtn = A[i * LD + j];
       lamw[e] = lam[e] + mu * (rtn - rho);
       rtw[e] = rtn;
-      // Y_ij = X_ij - eps G_ij[rho], G entry (a,b),(c,d) = rho_{(a,d),(b,c)}; Y_ji = Y_ij^T
-      const double y = Xs[e] - eps * R[(pa * m + pd) * D + (pb * m + pc)];
+      // Y_ij = X_ij - eps G_ij[rho], G entry (a,b),(c,d) = rho_{(a,d),(b,c)} (times the parity
+      // sign for fermions); Y_ji = Y_ij^T
+      T g = R[(pa * m + pd) * D + (pb * m + pc)];
+      if (a.fermionic && parity_odd(pa, pc, pd)) g = -g;
+      const double y = Xs[e] - eps * g;
       Yij[(size_t)i * n + j] = y;
       Yji[(size_t)j * n + i] = y;
       rr += (rho - rtn) * (rho - rtn);
@@ -400,7 +418,12 @@ __global__ void __launch_bounds__(GroupShape<D>::NT, GroupShape<D>::MINB) k5_bou
     for (int e = tid; e < D * D; e += NT) {
       const int i = e / D, j = e % D;
       const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
-      double k = Hb[e] - Xs[(pa * m + pc) * D + (pd * m + pb)] - Xs[(pc * m + pa) * D + (pb * m + pd)];
+      double x1 = Xs[(pa * m + pc) * D + (pd * m + pb)], x2 = Xs[(pc * m + pa) * D + (pb * m + pd)];
+      if (a.fermionic) {
+        if (parity_odd(pa, pd, pb)) x1 = -x1;
+        if (parity_odd(pc, pb, pd)) x2 = -x2;
+      }
+      double k = Hb[e] - x1 - x2;
       if (pb == pd) k += l1[pa * m + pc];
       if (pa == pc) k += l2[pb * m + pd];
       A[i * LD + j] = k;
@@ -570,6 +593,7 @@ struct ve_general {
   GenStatus *dst = nullptr, *hst = nullptr;
   DenseWs dws, bws;  // X-step eigensolver; the bound's eigensolve of X
   bool pair_warm = false;
+  int fermionic = 0;
   long projections = 0;
   // profiling: 0 pair pass, 1 cluster + dual + status, 2 dense eigensolve, 3 reconstruction
   bool prof = false;
@@ -630,6 +654,7 @@ GenArgs gen_args(ve_general* h) {
   a.parti = h->parti;
   a.vstore = h->vstore;
   a.warm = h->pair_warm ? 1 : 0;
+  a.fermionic = h->fermionic;
   a.st = h->dst;
   return a;
 }
@@ -714,34 +739,87 @@ void reset_status(ve_general* h) {
   *h->hst = g;
 }
 
+int check_shape(int N, int L) {
+  if (L < 1 || N < 2) return VE_EINVAL;
+  if (L > 3) return VE_EUNSUPPORTED;
+  if ((long)N * (1 << (2 * L)) > DENSE_MAX_N) return VE_EUNSUPPORTED;
+  return VE_OK;
+}
+
+int check_options(const ve_options* opt, ve_options& o) {
+  ve_default_options(&o);
+  if (opt) o = *opt;
+  if (!(o.mu > 0) || !(o.nu > 0) || !(o.eps > 0) || o.check_every < 1) return VE_EINVAL;
+  if (o.precision != VE_PREC_FP64) return VE_EUNSUPPORTED;
+  return VE_OK;
+}
+
+// Jordan-Wigner images on nb sites in a fixed order (position 0 the most significant bit of a
+// basis index, a site's bit set when it is occupied): a_p^dagger = Z ... Z sigma^- at position p,
+// Z = diag(1, -1) on every earlier position.  Terms are added into out (2^nb x 2^nb).
+int parity_before(int x, int nb, int p) {
+  const int before = ((1 << nb) - 1) & ~((1 << (nb - p)) - 1);  // positions 0 .. p-1
+  return __builtin_popcount((unsigned)(x & before)) & 1;
+}
+
+// t (a_p^dagger a_q + a_q^dagger a_p), p != q: each product applied to every basis state.
+void jw_add_hop(double* out, int nb, int p, int q, double t) {
+  const int dim = 1 << nb;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int pc = dir ? q : p, pa = dir ? p : q;  // created, annihilated position
+    const int bc = 1 << (nb - 1 - pc), ba = 1 << (nb - 1 - pa);
+    for (int x = 0; x < dim; ++x) {
+      if (!(x & ba) || (x & bc)) continue;
+      const int y = x & ~ba;  // after a_pa: sign of the occupied positions before pa in x
+      const int z = y | bc;   // after a_pc^dagger: those before pc in y
+      const int odd = parity_before(x, nb, pa) ^ parity_before(y, nb, pc);
+      out[(size_t)z * dim + x] += odd ? -t : t;
+    }
+  }
+}
+
+// v (n_p - 1/2)(n_q - 1/2): diagonal.
+void jw_add_density(double* out, int nb, int p, int q, double v) {
+  const int dim = 1 << nb;
+  for (int x = 0; x < dim; ++x) {
+    const double np = ((x >> (nb - 1 - p)) & 1) - 0.5, nq = ((x >> (nb - 1 - q)) & 1) - 0.5;
+    out[(size_t)x * dim + x] += v * np * nq;
+  }
+}
+
+int create_from_blocks(int N, int L, std::vector<double>& Hi, std::vector<double>& Hij, int fermionic,
+                       const ve_options& o, ve_general** out);
+void spin_blocks(const ve_terms* t, int L, std::vector<double>& Hi, std::vector<double>& Hij);
+int check_spin_terms(const ve_terms* t, int L);
+
 }  // namespace
 
 extern "C" {
 
 int ve_general_create(const ve_terms* t, int cluster_spins, const ve_options* opt, ve_general** out) {
-  if (!t || !out) return VE_EINVAL;
+  if (!out) return VE_EINVAL;
   *out = nullptr;
   const int L = cluster_spins;
-  if (L < 1 || t->nspins < 2 * L || t->nspins % L != 0 || t->nbond < 0) return VE_EINVAL;
-  if (t->nbond > 0 && (!t->bond_sites || !t->bond_ops)) return VE_EINVAL;
-  if (L > 3) return VE_EUNSUPPORTED;
-  const int N = t->nspins / L, m = 1 << L, D = m * m;
-  const long n = (long)N * D;
-  if (n > DENSE_MAX_N) return VE_EUNSUPPORTED;
-  for (int b = 0; b < t->nbond; ++b) {
-    const int s0 = t->bond_sites[2 * b], s1 = t->bond_sites[2 * b + 1];
-    if (s0 < 0 || s1 < 0 || s0 >= t->nspins || s1 >= t->nspins || s0 == s1) return VE_EINVAL;
-  }
+  int rc = check_spin_terms(t, L);
+  if (rc != VE_OK) return rc;
   ve_options o;
-  ve_default_options(&o);
-  if (opt) o = *opt;
-  if (!(o.mu > 0) || !(o.nu > 0) || !(o.eps > 0) || o.check_every < 1) return VE_EINVAL;
-  if (o.precision != VE_PREC_FP64) return VE_EUNSUPPORTED;
+  if ((rc = check_options(opt, o)) != VE_OK) return rc;
+  std::vector<double> Hi, Hij;
+  spin_blocks(t, L, Hi, Hij);
+  return create_from_blocks(t->nspins / L, L, Hi, Hij, 0, o, out);
+}
 
+}  // extern "C"
+
+namespace {
+
+// Cluster blocks of spin terms (Sec. 2.1 pairwise form): a term inside cluster c goes to H_c, a
+// term between clusters c < c' to H_cc' with cluster c the first factor.
+void spin_blocks(const ve_terms* t, int L, std::vector<double>& Hi, std::vector<double>& Hij) {
+  const int N = t->nspins / L, m = 1 << L, D = m * m;
   const long K = (long)N * (N - 1) / 2;
-  // cluster blocks (Sec. 2.1 pairwise form): a term inside cluster c goes to H_c, a term
-  // between clusters c < c' to H_cc' with cluster c the first factor
-  std::vector<double> Hi((size_t)N * m * m, 0.0), Hij((size_t)K * D * D, 0.0);
+  Hi.assign((size_t)N * m * m, 0.0);
+  Hij.assign((size_t)K * D * D, 0.0);
   for (int sp = 0; sp < t->nspins; ++sp) {
     if (!t->onsite) break;
     const int pos = sp % L;
@@ -762,6 +840,117 @@ int ve_general_create(const ve_terms* t, int cluster_spins, const ve_options* op
       embed(B, 2, pos, 2 * L, Hij.data() + (size_t)pair_index(N, c1, c0) * D * D);
     }
   }
+}
+
+// Eq. (sdpFerm): H_c is the Jordan-Wigner image of the terms inside cluster c in the cluster's
+// site order; H_cc' (c < c') that of the terms between the two clusters, c's sites first.
+void fermion_blocks(const ve_fermion_terms* t, int L, std::vector<double>& Hi, std::vector<double>& Hij) {
+  const int N = t->nsites / L, m = 1 << L, D = m * m;
+  const long K = (long)N * (N - 1) / 2;
+  Hi.assign((size_t)N * m * m, 0.0);
+  Hij.assign((size_t)K * D * D, 0.0);
+  for (int k = 0; k < t->nhop + t->npair; ++k) {
+    const bool hop = k < t->nhop;
+    const int* st = hop ? t->hop_sites + 2 * k : t->pair_sites + 2 * (k - t->nhop);
+    const double c = hop ? t->hop_t[k] : t->pair_v[k - t->nhop];
+    const int s0 = st[0], s1 = st[1], c0 = s0 / L, c1 = s1 / L;
+    double* blk;
+    int nb, p0, p1;
+    if (c0 == c1) {
+      blk = Hi.data() + (size_t)c0 * m * m;
+      nb = L;
+      p0 = s0 % L;
+      p1 = s1 % L;
+    } else {
+      const int g = c0 < c1 ? c0 : c1, d = c0 < c1 ? c1 : c0;
+      blk = Hij.data() + (size_t)pair_index(N, g, d) * D * D;
+      nb = 2 * L;
+      p0 = (c0 == g ? 0 : L) + s0 % L;
+      p1 = (c1 == g ? 0 : L) + s1 % L;
+    }
+    if (hop) {
+      jw_add_hop(blk, nb, p0, p1, c);
+    } else {
+      jw_add_density(blk, nb, p0, p1, c);
+    }
+  }
+}
+
+int check_fermion_terms(const ve_fermion_terms* t, int L) {
+  if (!t || L < 1 || t->nsites < 2 * L || t->nsites % L != 0 || t->nhop < 0 || t->npair < 0)
+    return VE_EINVAL;
+  if ((t->nhop > 0 && (!t->hop_sites || !t->hop_t)) || (t->npair > 0 && (!t->pair_sites || !t->pair_v)))
+    return VE_EINVAL;
+  const int rc = check_shape(t->nsites / L, L);
+  if (rc != VE_OK) return rc;
+  for (int k = 0; k < t->nhop + t->npair; ++k) {
+    const int* st = k < t->nhop ? t->hop_sites + 2 * k : t->pair_sites + 2 * (k - t->nhop);
+    if (st[0] < 0 || st[1] < 0 || st[0] >= t->nsites || st[1] >= t->nsites || st[0] == st[1])
+      return VE_EINVAL;
+  }
+  return VE_OK;
+}
+
+int check_spin_terms(const ve_terms* t, int L) {
+  if (!t || L < 1 || t->nspins < 2 * L || t->nspins % L != 0 || t->nbond < 0) return VE_EINVAL;
+  if (t->nbond > 0 && (!t->bond_sites || !t->bond_ops)) return VE_EINVAL;
+  const int rc = check_shape(t->nspins / L, L);
+  if (rc != VE_OK) return rc;
+  for (int b = 0; b < t->nbond; ++b) {
+    const int s0 = t->bond_sites[2 * b], s1 = t->bond_sites[2 * b + 1];
+    if (s0 < 0 || s1 < 0 || s0 >= t->nspins || s1 >= t->nspins || s0 == s1) return VE_EINVAL;
+  }
+  return VE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ve_spin_blocks(const ve_terms* terms, int cluster_spins, double* Hi, double* Hij) {
+  if (!Hi || !Hij) return VE_EINVAL;
+  const int rc = check_spin_terms(terms, cluster_spins);
+  if (rc != VE_OK) return rc;
+  std::vector<double> a, b;
+  spin_blocks(terms, cluster_spins, a, b);
+  memcpy(Hi, a.data(), a.size() * sizeof(double));
+  memcpy(Hij, b.data(), b.size() * sizeof(double));
+  return VE_OK;
+}
+
+int ve_fermion_blocks(const ve_fermion_terms* terms, int cluster_sites, double* Hi, double* Hij) {
+  if (!Hi || !Hij) return VE_EINVAL;
+  const int rc = check_fermion_terms(terms, cluster_sites);
+  if (rc != VE_OK) return rc;
+  std::vector<double> a, b;
+  fermion_blocks(terms, cluster_sites, a, b);
+  memcpy(Hi, a.data(), a.size() * sizeof(double));
+  memcpy(Hij, b.data(), b.size() * sizeof(double));
+  return VE_OK;
+}
+
+int ve_general_create_fermions(const ve_fermion_terms* t, int cluster_sites, const ve_options* opt,
+                               ve_general** out) {
+  if (!out) return VE_EINVAL;
+  *out = nullptr;
+  int rc = check_fermion_terms(t, cluster_sites);
+  if (rc != VE_OK) return rc;
+  ve_options o;
+  if ((rc = check_options(opt, o)) != VE_OK) return rc;
+  std::vector<double> Hi, Hij;
+  fermion_blocks(t, cluster_sites, Hi, Hij);
+  return create_from_blocks(t->nsites / cluster_sites, cluster_sites, Hi, Hij, 1, o, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int create_from_blocks(int N, int L, std::vector<double>& Hi, std::vector<double>& Hij, int fermionic,
+                       const ve_options& o, ve_general** out) {
+  const int m = 1 << L, D = m * m;
+  const long n = (long)N * D;
+  const long K = (long)N * (N - 1) / 2;
   std::vector<int> pi(K), pj(K);
   for (int i = 0, p = 0; i < N; ++i)
     for (int j = i + 1; j < N; ++j, ++p) {
@@ -778,6 +967,7 @@ int ve_general_create(const ve_terms* t, int cluster_spins, const ve_options* op
   h->n = (int)n;
   h->K = K;
   h->opt = o;
+  h->fermionic = fermionic;
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
     return VE_ECUDA;
@@ -860,6 +1050,10 @@ int ve_general_create(const ve_terms* t, int cluster_spins, const ve_options* op
   *out = h;
   return VE_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 void ve_general_destroy(ve_general* h) {
   if (!h) return;

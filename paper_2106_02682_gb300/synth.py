@@ -9,7 +9,9 @@ Only random-matrix and workload generators live here (no step of the solver's ar
   * workloads: the named benchmark instances (lattice, cluster, field) used by bench.py;
   * batch_instances: seeded families of independent instances for batched runs;
   * disordered_chain: a general (not translation-invariant) spin chain as a list of terms, the
-    input of the general solver: random fields and long-range random couplings.
+    input of the general solver: random fields and long-range random couplings;
+  * fermion_ring: the spinless-fermion ring of the paper's fermionic section as hopping and
+    density-density terms.
 The default seed is 20210604.
 """
 import numpy as np
@@ -169,3 +171,18 @@ def disordered_chain(nspins, kind="tfim", alpha=2.0, seed=None, field=(0.5, 1.5)
         ops = J[:, None, None] * (np.kron(_PX, _PX) + _PYPY
                                   + delta[sites[:, 0], None, None] * np.kron(_PZ, _PZ))
     return dict(nspins=nspins, onsite=onsite, bond_sites=sites, bond_ops=ops)
+
+
+def fermion_ring(nsites, U, long_range=False):
+    """Spinless fermions on a periodic ring (the paper's fermionic examples): hopping -1 on each
+    ring bond, and U (n_i - 1/2)(n_j - 1/2) on each bond, or, long-range, U / d(i, j) for every
+    ordered pair i != j (2 U / d per unordered pair, d the distance on the ring).
+    Returns dict(nsites, hops [(i, j, t)], pairs [(i, j, v)]) with i < j."""
+    bonds = sorted({tuple(sorted((i, (i + 1) % nsites))) for i in range(nsites)})
+    hops = [(i, j, -1.0) for i, j in bonds]
+    if long_range:
+        pairs = [(i, j, 2.0 * U / min(j - i, nsites - (j - i)))
+                 for i in range(nsites) for j in range(i + 1, nsites)]
+    else:
+        pairs = [(i, j, float(U)) for i, j in bonds]
+    return dict(nsites=nsites, hops=hops, pairs=pairs)

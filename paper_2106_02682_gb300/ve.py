@@ -77,6 +77,11 @@ class ve_terms(ctypes.Structure):
                 ("bond_sites", c_void_p), ("bond_ops", c_void_p)]
 
 
+class ve_fermion_terms(ctypes.Structure):
+    _fields_ = [("nsites", c_int), ("nhop", c_int), ("hop_sites", c_void_p), ("hop_t", c_void_p),
+                ("npair", c_int), ("pair_sites", c_void_p), ("pair_v", c_void_p)]
+
+
 class VEError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -140,6 +145,10 @@ def _load():
                                                  c_int, c_int, c_void_p]),
         "ve_general_create": (c_int, [ctypes.POINTER(ve_terms), c_int, ctypes.POINTER(ve_options),
                                       ctypes.POINTER(c_void_p)]),
+        "ve_general_create_fermions": (c_int, [ctypes.POINTER(ve_fermion_terms), c_int,
+                                               ctypes.POINTER(ve_options), ctypes.POINTER(c_void_p)]),
+        "ve_spin_blocks": (c_int, [ctypes.POINTER(ve_terms), c_int, P_double, P_double]),
+        "ve_fermion_blocks": (c_int, [ctypes.POINTER(ve_fermion_terms), c_int, P_double, P_double]),
         "ve_general_destroy": (None, [c_void_p]),
         "ve_general_dims": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                     ctypes.POINTER(c_int), ctypes.POINTER(c_long)]),
@@ -452,9 +461,9 @@ def ve_mlp_predict(m, x, n_out):
 
 
 # ---- general Hamiltonians (Algorithm 5) ------------------------------------------------------
-def ve_general_create(terms, cluster_spins, opt=None):
-    """terms: dict(nspins, onsite (nspins, 2, 2) or None, bond_sites (nb, 2), bond_ops (nb, 4, 4)).
-    Returns a handle (int)."""
+def _spin_terms(terms):
+    """ve_terms for dict(nspins, onsite (nspins, 2, 2) or None, bond_sites (nb, 2),
+    bond_ops (nb, 4, 4)); the arrays it points to are returned with it to keep them alive."""
     nspins = int(terms["nspins"])
     onsite = terms.get("onsite")
     on = None if onsite is None else np.ascontiguousarray(onsite, dtype=np.float64).reshape(nspins, 4)
@@ -462,10 +471,65 @@ def ve_general_create(terms, cluster_spins, opt=None):
     ops = np.ascontiguousarray(terms["bond_ops"], dtype=np.float64).reshape(-1, 16)
     t = ve_terms(nspins, on.ctypes.data if on is not None else None, sites.shape[0],
                  sites.ctypes.data if sites.size else None, ops.ctypes.data if ops.size else None)
+    return t, (on, sites, ops)
+
+
+def _fermion_terms(terms):
+    """ve_fermion_terms for dict(nsites, hops [(i, j, t)], pairs [(i, j, v)])."""
+    hops = list(terms.get("hops", ()))
+    pairs = list(terms.get("pairs", ()))
+    hs = np.ascontiguousarray([(i, j) for i, j, _ in hops], dtype=np.int32).reshape(-1, 2)
+    ht = np.ascontiguousarray([t for _, _, t in hops], dtype=np.float64)
+    ps = np.ascontiguousarray([(i, j) for i, j, _ in pairs], dtype=np.int32).reshape(-1, 2)
+    pv = np.ascontiguousarray([v for _, _, v in pairs], dtype=np.float64)
+    t = ve_fermion_terms(int(terms["nsites"]), len(hops), hs.ctypes.data if hops else None,
+                         ht.ctypes.data if hops else None, len(pairs),
+                         ps.ctypes.data if pairs else None, pv.ctypes.data if pairs else None)
+    return t, (hs, ht, ps, pv)
+
+
+def ve_general_create(terms, cluster_spins, opt=None):
+    """terms: dict(nspins, onsite (nspins, 2, 2) or None, bond_sites (nb, 2), bond_ops (nb, 4, 4)).
+    Returns a handle (int)."""
+    t, keep = _spin_terms(terms)
     h = c_void_p()
     _check(_lib.ve_general_create(ctypes.byref(t), int(cluster_spins),
                                   ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)),
            "ve_general_create")
+    return h.value
+
+
+def _blocks(fn, t, n_units, L, name):
+    m = 2 ** L
+    N = n_units // L
+    K = N * (N - 1) // 2
+    Hi = np.zeros((N, m, m))
+    Hij = np.zeros((K, m * m, m * m))
+    _check(fn(ctypes.byref(t), int(L), Hi.ctypes.data_as(P_double), Hij.ctypes.data_as(P_double)),
+           name)
+    return Hi, Hij
+
+
+def ve_spin_blocks(terms, cluster_spins):
+    """(Hi (N, m, m), Hij (K, D, D)) that ve_general_create builds, on the host."""
+    t, keep = _spin_terms(terms)
+    return _blocks(_lib.ve_spin_blocks, t, int(terms["nspins"]), cluster_spins, "ve_spin_blocks")
+
+
+def ve_fermion_blocks(terms, cluster_sites):
+    """(Hi, Hij) that ve_general_create_fermions builds, on the host."""
+    t, keep = _fermion_terms(terms)
+    return _blocks(_lib.ve_fermion_blocks, t, int(terms["nsites"]), cluster_sites,
+                   "ve_fermion_blocks")
+
+
+def ve_general_create_fermions(terms, cluster_sites, opt=None):
+    """terms: dict(nsites, hops [(i, j, t)], pairs [(i, j, v)]).  Returns a handle (int)."""
+    t, keep = _fermion_terms(terms)
+    h = c_void_p()
+    _check(_lib.ve_general_create_fermions(ctypes.byref(t), int(cluster_sites),
+                                           ctypes.byref(opt) if opt is not None else None,
+                                           ctypes.byref(h)), "ve_general_create_fermions")
     return h.value
 
 

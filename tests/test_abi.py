@@ -44,7 +44,8 @@ def test_struct_layouts_match_the_header(ve, tmp_path):
     """Compile a C probe against include/ve.h and compare sizes/offsets with the ctypes mirror."""
     structs = {"ve_lattice": ve.ve_lattice, "ve_cluster": ve.ve_cluster,
                "ve_hamiltonian": ve.ve_hamiltonian, "ve_options": ve.ve_options,
-               "ve_status": ve.ve_status, "ve_cert": ve.ve_cert, "ve_terms": ve.ve_terms}
+               "ve_status": ve.ve_status, "ve_cert": ve.ve_cert, "ve_terms": ve.ve_terms,
+               "ve_fermion_terms": ve.ve_fermion_terms}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ve.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
@@ -162,3 +163,43 @@ def test_general_null_handles_and_dense_workspace_sizes(ve):
         assert (ve.ve_project_psd_dense_workspace_size(n) > 0) == ok, n
     # two n x n float64 matrices plus small vectors
     assert ve.ve_project_psd_dense_workspace_size(512) >= 2 * 512 * 512 * 8
+
+
+@pytest.mark.parametrize("nspins,L,kind", [(6, 1, "tfim"), (8, 2, "xxz"), (9, 3, "tfim")])
+def test_host_spin_blocks_match_the_oracle(ve, nspins, L, kind):
+    from oracle import models
+    from paper_2106_02682_gb300 import synth
+    terms = synth.disordered_chain(nspins, kind, alpha=1.5, seed=nspins)
+    bonds = [(int(s), int(t), B) for (s, t), B in zip(terms['bond_sites'], terms['bond_ops'])]
+    ref = models.general_blocks(nspins, L, terms['onsite'], bonds)
+    Hi, Hij = ve.ve_spin_blocks(terms, L)
+    np.testing.assert_allclose(Hi, ref['Hi'], atol=1e-14)
+    np.testing.assert_allclose(Hij, ref['Hij'], atol=1e-14)
+
+
+@pytest.mark.parametrize("M,L,U,lr", [(6, 1, 1.5, False), (8, 2, 2.0, False), (8, 2, 1.0, True),
+                                      (9, 3, 0.7, True), (12, 2, 0.0, False)])
+def test_host_fermion_blocks_match_the_oracle(ve, M, L, U, lr):
+    # the library enumerates basis states with explicit string signs, the oracle multiplies
+    # Kronecker-product creation operators: two independent Jordan-Wigner constructions
+    from oracle import fermions
+    from paper_2106_02682_gb300 import synth
+    terms = synth.fermion_ring(M, U, long_range=lr)
+    oh, op = fermions.ring_terms(M, U, long_range=lr)
+    assert [tuple(x) for x in terms['hops']] == [tuple(x) for x in oh]
+    assert [tuple(x) for x in terms['pairs']] == pytest.approx([tuple(x) for x in op])
+    ref = fermions.fermion_blocks(M, L, U, long_range=lr)
+    Hi, Hij = ve.ve_fermion_blocks(terms, L)
+    np.testing.assert_allclose(Hi, ref['Hi'], atol=1e-14)
+    np.testing.assert_allclose(Hij, ref['Hij'], atol=1e-14)
+
+
+def test_fermion_create_rejects_bad_terms_before_touching_the_gpu(ve):
+    for terms, L, code in ((dict(nsites=8, hops=[(0, 0, -1.0)]), 2, -1),
+                           (dict(nsites=8, hops=[(0, 8, -1.0)]), 2, -1),
+                           (dict(nsites=7, hops=[(0, 1, -1.0)]), 2, -1),
+                           (dict(nsites=8, hops=[(0, 1, -1.0)]), 4, -5),
+                           (dict(nsites=272, hops=[(0, 1, -1.0)]), 1, -5)):
+        with pytest.raises(ve.VEError) as ei:
+            ve.ve_general_create_fermions(terms, L)
+        assert ei.value.code == code

@@ -222,3 +222,48 @@ def test_general_full_size_workload_matches_the_oracle(ve):
                                                  abs=tol(n))
     finally:
         ve.ve_general_destroy(h)
+
+
+# ------------------------------------------------------------------ spinless fermions
+FERMION_CASES = [
+    # (sites, sites per cluster, U, long range, sweeps)
+    (8, 2, 2.0, False, 10),
+    (12, 2, 1.0, True, 6),
+    (9, 3, 0.7, True, 4),
+]
+
+
+@pytest.mark.parametrize("M,L,U,lr,sweeps", FERMION_CASES)
+def test_fermion_sweeps_match_the_oracle(ve, M, L, U, lr, sweeps):
+    from oracle import fermions
+    blocks = fermions.fermion_blocks(M, L, U, long_range=lr)
+    pb = alg5.GeneralProblem(blocks, fermionic=True)
+    s5 = alg5.general_setup(blocks)
+    st = alg5.initial_state(pb, s5)
+    h = ve.ve_general_create_fermions(synth.fermion_ring(M, U, long_range=lr), L)
+    try:
+        n = pb.N * pb.D
+        for k in range(sweeps):
+            diag = alg5.iterate(pb, s5, st)
+            code, gs = ve.ve_general_iterate(h, 1)
+            assert gs.energy_per_spin == pytest.approx(diag['energy'], abs=tol(n))
+            assert gs.feas_err == pytest.approx(diag['feas_err'], rel=tol(n), abs=1e-14)
+        assert relerr(ve.ve_general_get_state(h), alg5.pack_state(pb, s5, st)) < tol(n)
+        c = ve.ve_general_bound(h)
+        assert c.bound_per_spin == pytest.approx(alg5.certified_bound(pb, s5, st)['bound_per_spin'],
+                                                 abs=tol(n))
+    finally:
+        ve.ve_general_destroy(h)
+
+
+def test_fermion_relaxation_is_exact_at_zero_interaction_on_the_gpu(ve):
+    from oracle import fermions
+    M = 12
+    h = ve.ve_general_create_fermions(synth.fermion_ring(M, 0.0), 2)
+    try:
+        code, st = ve.ve_general_iterate(h, 4000, 1e-11)
+        assert code == ve.VE_OK
+        assert M * st.energy_per_spin == pytest.approx(fermions.free_fermion_energy(M), abs=1e-8)
+        assert M * ve.ve_general_bound(h).bound_per_spin <= fermions.free_fermion_energy(M) + 1e-9
+    finally:
+        ve.ve_general_destroy(h)
