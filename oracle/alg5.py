@@ -38,14 +38,16 @@ class GeneralProblem:
 
 def _G_pair(pb, rho):
     """Off-diagonal blocks of the global matrix (with the fermionic parity signs if any)."""
+    sign = getattr(pb, 'sign', None)   # translation-invariant problems carry none
     g = G_pair(rho)
-    return g if pb.sign is None else pb.sign * g
+    return g if sign is None else sign * g
 
 
 def _eff_ham_pair(pb, H, Xij):
     """H'_ij of Eq. (effHam): H minus the adjoint of the off-diagonal G map applied to X_ij (and
     its transpose); the signed map's adjoint applies the same signs to X first."""
-    return eff_ham_pair(H, Xij if pb.sign is None else pb.sign * Xij)
+    sign = getattr(pb, 'sign', None)
+    return eff_ham_pair(H, Xij if sign is None else sign * Xij)
 
 
 def general_setup(blocks):
