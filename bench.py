@@ -666,12 +666,26 @@ def general_oracle(name):
     from oracle import alg5
     from oracle import models as mo
     from paper_2106_02682_gb300 import synth
-    terms, L = synth.general_terms(name)
-    bonds = [(int(s), int(t), B) for (s, t), B in zip(terms["bond_sites"], terms["bond_ops"])]
-    blocks = mo.general_blocks(terms["nspins"], L, terms["onsite"], bonds)
-    pb = alg5.GeneralProblem(blocks)
+    w = synth.GENERAL_WORKLOADS[name]
+    if w["kind"] == "fermion":
+        from oracle import fermions
+        blocks = fermions.fermion_blocks(w["nsites"], w["L"], w["U"], long_range=w["long_range"])
+        pb = alg5.GeneralProblem(blocks, fermionic=True)
+    else:
+        terms, L = synth.general_terms(name)
+        bonds = [(int(s), int(t), B) for (s, t), B in zip(terms["bond_sites"], terms["bond_ops"])]
+        blocks = mo.general_blocks(terms["nspins"], L, terms["onsite"], bonds)
+        pb = alg5.GeneralProblem(blocks)
     s5 = alg5.general_setup(blocks)
     return alg5, pb, s5, alg5.initial_state(pb, s5)
+
+
+def general_create(ve, terms, L, opt):
+    """A general handle for spin terms (ve_general_create) or fermion terms
+    (ve_general_create_fermions)."""
+    if "nsites" in terms:
+        return ve.ve_general_create_fermions(terms, L, opt)
+    return ve.ve_general_create(terms, L, opt)
 
 
 def general_oracle_rate(name, seconds):
@@ -693,7 +707,7 @@ def general_rate(ve, synth, name, warmup, steps, stream, flush):
     per-stage times, the X step's Jacobi sweeps, and the roofline of its round kernel."""
     import torch
     terms, L = synth.general_terms(name)
-    h = ve.ve_general_create(terms, L, ve.ve_default_options(stream=stream.cuda_stream))
+    h = general_create(ve, terms, L, ve.ve_default_options(stream=stream.cuda_stream))
     try:
         N, m, D, K = ve.ve_general_dims(h)
         n = N * D
@@ -731,7 +745,8 @@ def general_rate(ve, synth, name, warmup, steps, stream, flush):
     achieved = flops_round / (ms_round * 1e-3) / 1e12
     xstep_ms = (pms[2] + pms[3]) / k_prof
     return {
-        "value": steps / (ms * 1e-3), "ms_per_step": ms / steps, "nspins": terms["nspins"],
+        "value": steps / (ms * 1e-3), "ms_per_step": ms / steps,
+        "nspins": terms.get("nspins", terms.get("nsites")),
         "clusters": N, "pair_dim": D, "pairs": K, "x_dim": n,
         "launches_per_sweep": sum(pl) / k_prof, "stages": stages,
         "jacobi_sweeps_per_x_step": jac, "x_steps_first_order": first_order / k_prof,
@@ -762,7 +777,7 @@ def run_general(args):
     ck = clocks.stop()
     # end to end through the public API with host buffers
     terms, L = synth.general_terms(args.workload)
-    h = ve.ve_general_create(terms, L, ve.ve_default_options(stream=stream.cuda_stream))
+    h = general_create(ve, terms, L, ve.ve_default_options(stream=stream.cuda_stream))
     try:
         ve.ve_general_iterate(h, 3)
         sb = ve.ve_general_state_size(h)
@@ -784,7 +799,9 @@ def run_general(args):
         "metric": "Algorithm 5 ADMM sweeps/s (general Hamiltonian, dense X step)", "value": g["value"],
         "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": g["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded disordered long-range spin chain, no dataset)",
+        "data": ("synthetic (spinless-fermion ring of the paper's fermionic section, no dataset)"
+                 if w["kind"] == "fermion" else
+                 "synthetic (seeded disordered long-range spin chain, no dataset)"),
         "config": {"workload": args.workload, **w, "clusters": g["clusters"], "pairs": g["pairs"],
                    "pair_dim": g["pair_dim"], "x_dim": g["x_dim"], "mu": 10.0, "nu": 10.0,
                    "eps": 2.0, "l2": "flushed (512 MB write) before every timed step",
@@ -829,7 +846,8 @@ def run_general_reference(args):
 
 def main():
     args = parse()
-    general = args.workload.startswith(("lrtfim", "lrxxz"))
+    from paper_2106_02682_gb300 import synth
+    general = args.workload in synth.GENERAL_WORKLOADS
     if args.impl == "reference":
         if general:
             if dist_env()[1] == 0:

@@ -140,11 +140,19 @@ GENERAL_WORKLOADS = {
     # disordered XXZ chain of 64 spins, all-to-all 1/r^2, 2-spin clusters: 496 pairs of 16 x 16
     # marginals, X of 512 x 512
     "lrxxz_N64_L2": dict(nspins=64, L=2, kind="xxz", alpha=2.0),
+    # the paper's fermionic benchmarks: spinless fermions on a 20-site ring, 2-site clusters
+    # (45 pairs of 16 x 16 marginals, X of 160 x 160), short-range U = 2 and long-range U = 1
+    "sf_N20_L2": dict(nsites=20, L=2, kind="fermion", U=2.0, long_range=False),
+    "lrsf_N20_L2": dict(nsites=20, L=2, kind="fermion", U=1.0, long_range=True),
 }
 
 
 def general_terms(name):
+    """(terms, sites per cluster) of a general workload: spin terms (dict with nspins) or
+    spinless-fermion terms (dict with nsites)."""
     w = GENERAL_WORKLOADS[name]
+    if w["kind"] == "fermion":
+        return fermion_ring(w["nsites"], w["U"], long_range=w["long_range"]), w["L"]
     return disordered_chain(w["nspins"], w["kind"], alpha=w["alpha"]), w["L"]
 
 
