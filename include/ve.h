@@ -429,7 +429,9 @@ int ve_general_profile_rounds(ve_general* h, double* ms, long* rounds, long* fir
  * general solver's X step always does this).  Every Jacobi round is one launch over n/2 CTAs;
  * the n - 1 rounds of a sweep are one CUDA graph.  *sweeps (may be NULL) receives the Jacobi
  * sweeps taken, plus 1000 if the first-order reconstruction was used.  Synchronises `stream`
- * (once per Jacobi sweep).  Errors: VE_EINVAL (NULL, n, workspace, flags), VE_ECUDA. */
+ * (once per Jacobi sweep).  Each call captures and instantiates the graph of a sweep's n - 1
+ * round launches anew (milliseconds for n = 512); a ve_general handle keeps its graph.
+ * Errors: VE_EINVAL (NULL, n, workspace, flags), VE_ECUDA. */
 #define VE_DENSE_WARM 1
 #define VE_DENSE_FIRST_ORDER 2
 size_t ve_project_psd_dense_workspace_size(int n);

@@ -2,6 +2,7 @@
 sharded): every rank times its own replica and the job takes as long as the slowest rank.  This
 checks that bookkeeping with two gloo ranks on the CPU, and that the reference arm runs on rank
 0 only."""
+import json
 import os
 import socket
 import subprocess
@@ -65,3 +66,17 @@ def test_reference_arm_runs_on_rank_zero_only():
     outs = _launch(code, 2)
     assert '"impl": "reference"' in outs[0]
     assert outs[1].strip() == ""
+
+
+@pytest.mark.parametrize("workload", ["sf_N20_L2", "lrtfim_N128_L1"])
+def test_reference_arm_of_the_general_workloads(workload):
+    # the oracle's Algorithm 5 (spin terms, or the fermionic relaxation) as the reference arm
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); sys.argv = ['bench.py', '--impl', "
+            f"'reference', '--steps', '1', '--warmup', '0', '--workload', {workload!r}]; "
+            "import bench; bench.main()")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                         timeout=240)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle"
