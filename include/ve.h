@@ -383,7 +383,10 @@ int ve_general_dims(const ve_general* h, int* N, int* m, int* D, long* K);
  * (sum_i Tr[H_i rho_i] + sum_{i<j} Tr[H_ij rho_ij]) / nspins with the closed-form pair
  * marginals, Eq. (feasErr) as sqrt(sum_{i<j} (|A1 rho_ij - rho_i|^2 + |A2 rho_ij - rho_j|^2 +
  * |rho_ij - rho~_ij|^2) / K), |energy change|, residual = max of the last two.  Synchronous
- * (the X step's eigensolve reads its stopping test on the host once per Jacobi sweep).
+ * (the X step's eigensolve reads its stopping test on the host once per Jacobi sweep).  The X
+ * step starts from the previous sweep's eigenvectors (from V = I on the first sweep and every
+ * 256th), and ends either by the exact stopping rule or, once A = V^T Y V is nearly diagonal,
+ * with the first-order reconstruction of VE_DENSE_FIRST_ORDER (below), equally accurate.
  * Returns as ve_iterate. */
 int ve_general_iterate(ve_general* h, long max_iter, double tol, ve_status* out);
 int ve_general_get_status(ve_general* h, ve_status* out);
