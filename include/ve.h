@@ -41,6 +41,7 @@ extern "C" {
 #define VE_ECUDA (-3)        /* a CUDA call failed                                        */
 #define VE_ENONFINITE (-4)   /* the iteration produced a NaN or Inf                       */
 #define VE_EUNSUPPORTED (-5) /* valid but not implemented here (e.g. cluster size)        */
+#define VE_ETIMEOUT (-6)     /* a bounded wait inside a kernel gave up; the result is invalid */
 
 #define VE_PREC_FP64 0  /* every step in float64                                          */
 #define VE_PREC_MIXED 1 /* float32 arithmetic in the pair pass, the block DFT and both PSD
@@ -187,6 +188,12 @@ int ve_profile_read(ve_handle* h, double* ms, long* launches);
 /* Mean Jacobi sweeps per eigensolve over the profiled sweeps: pair projections (*pair) and
  * wavevector projections (*wavevector); 0 if none ran.  Errors: VE_EINVAL, VE_ECUDA. */
 int ve_profile_sweeps(ve_handle* h, double* pair, double* wavevector);
+/* How many eigensolves of the profiled sweeps ended with the first-order (Daleckii-Krein)
+ * reconstruction instead of a converged Jacobi sweep -- the early stop of the projections of
+ * Eq. (rhoijTildeUpdate) and of Algorithm 6's per-wavevector step.  pair[0] / wavevector[0]
+ * receive those counts, pair[1] / wavevector[1] the eigensolves (two longs each, host).
+ * Errors: VE_EINVAL, VE_ECUDA. */
+int ve_profile_first_order(ve_handle* h, long* pair, long* wavevector);
 
 /* Name of a status code (static string). */
 const char* ve_error_string(int code);
@@ -299,13 +306,14 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
  * ve_circulant_workspace_size(dim, M, D) <= VE_NOALLOC_SCRATCH_BYTES, which admits every
  * first block row with N * D * D <= 2^20 float64 entries (e.g. 4096 clusters with D = 16);
  * larger requests return VE_EINVAL before any GPU work.
- *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress
- *     with that device current); make that first call before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress), so the address stays right after cudaDeviceReset.  The first call
+ *     on a device may load the library's device code there: make it before any stream capture.
  *   - All calls on a device share the one array and leave their data in it.  Calls whose GPU
  *     work overlaps (other streams, or other host threads, without ordering between them) race
  *     on it and produce wrong results; order them on one stream or with events.
  * Errors: VE_EINVAL (NULL pointers, bad sizes, request above the limit), VE_EUNSUPPORTED (as
- * for ve_circulant_project, or a device ordinal above 63), VE_ECUDA. */
+ * for ve_circulant_project), VE_ECUDA. */
 #define VE_NOALLOC_SCRATCH_BYTES ((size_t)(16u << 20) + (size_t)(256u << 10))
 int ve_circulant_project_noalloc(const double* x_in, double* x_out, int dim, const int M[2], int D,
                                  int precision, void* stream);

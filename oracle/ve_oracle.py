@@ -132,12 +132,38 @@ def T_inverse(Y, mu, nu):
     return (Y - P1 - P2 + Q) / mu + (P1 + P2 - 2 * Q) / (mu + a) + Q / (mu + 2 * a)
 
 
+def _proj_psd_one_thread(C):
+    w, V = np.linalg.eigh(C)
+    return (V * np.maximum(w, 0.0)[..., None, :]) @ np.conj(np.swapaxes(V, -1, -2))
+
+
+# Optional thread pool over the independent matrices of a batch (the pair offsets delta and the
+# wavevectors k of one sweep).  Every matrix still goes through the same eigh call on its own,
+# so the results do not depend on the number of threads; numpy releases the GIL inside LAPACK.
+_POOL = None
+_THREADS = 1
+
+
+def set_threads(n):
+    """Run the batched projections of a sweep on n host threads (1: no pool)."""
+    global _POOL, _THREADS
+    import concurrent.futures
+    if _POOL is not None:
+        _POOL.shutdown()
+        _POOL = None
+    _THREADS = max(1, int(n))
+    if _THREADS > 1:
+        _POOL = concurrent.futures.ThreadPoolExecutor(max_workers=_THREADS)
+
+
 def proj_psd(C):
     """Pi_{>=0}(C) (Sec. 3): nearest PSD matrix in Frobenius norm = eigendecomposition with
     negative eigenvalues set to zero.  Works batched, real symmetric or complex Hermitian
     (reading R5)."""
-    w, V = np.linalg.eigh(C)
-    return (V * np.maximum(w, 0.0)[..., None, :]) @ np.conj(np.swapaxes(V, -1, -2))
+    if _POOL is None or C.ndim < 3 or C.shape[0] < 2 * _THREADS:
+        return _proj_psd_one_thread(C)
+    parts = list(_POOL.map(_proj_psd_one_thread, np.array_split(C, _THREADS)))
+    return np.concatenate(parts)
 
 
 # ----------------------------------------------------------------------------------------

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libve_gb300.so")
 SOURCES = ["ve_sweep.cu", "ve_fft.cu", "ve_bound.cu", "ve_api.cu", "ve_noalloc.cu", "ve_mlp.cu",
-           "ve_dense.cu", "ve_general.cu"]
+           "ve_dense.cu", "ve_general.cu", "ve_tcgemm.cu", "ve_tcproj.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
@@ -65,7 +65,7 @@ def build(force=False, verbose=False, ptxas_info=False):
     objs = [os.path.join(OBJ, s.replace(".cu", ".o")) for s in SOURCES]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
+        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-Xlinker", "-z,defs"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

@@ -3,6 +3,8 @@
 // standalone batched entry points.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdint.h>
 #include <string.h>
 
@@ -192,8 +194,15 @@ struct ve_handle {
   bool prof = false;
   cudaEvent_t ev[VE_NSTAGE + 1] = {};
   double prof_ms[VE_NSTAGE] = {};
-  unsigned long long* jstats = nullptr;  // device: pair sweeps, pair matrices, k sweeps, k matrices
+  // device: pair sweeps, pair matrices, pair first-order stops, then the same for wavevectors
+  unsigned long long* jstats = nullptr;
   unsigned char* gws = nullptr;          // D = 256: staging workspace of the eigensolver kernels
+  // D = 256 in mixed precision: the float32 per-wavevector projections with their products on
+  // the tensor cores (ve_tcproj.cu); a separate allocation, made only for such handles
+  void* tcmem = nullptr;
+  TcProjWs tcx;         // the wavevector projections (complex, ncanon matrices)
+  TcProjWs tcp;         // the pair projections (real, Pc matrices)
+  float* rbuf = nullptr;  // rho of the pair pass, Pc * D * D floats
   long prof_launch[VE_NSTAGE] = {};
   int stage_launches[VE_NSTAGE] = {};
 };
@@ -208,6 +217,7 @@ namespace {
 
 PairArgs pair_args(ve_handle* h) {
   PairArgs a;
+  a.iter = &h->dst->iter;
   a.N = h->md.N;
   a.P = h->P;
   a.m = h->md.m;
@@ -269,6 +279,10 @@ cudaError_t issue_sweep(ve_handle* h, int arith, bool warm) {
   pa.warm = warm ? 1 : 0;
   pa.stats = h->prof ? h->jstats : nullptr;
   pa.gws = h->gws;
+  if (fp32 && h->tcmem) {
+    pa.tcw = &h->tcp;
+    pa.rbuf = h->rbuf;
+  }
   const SmallArgs sa = small_args(h);
   cudaError_t e;
   if (!warm && !h->fft_tuned[fp32 ? 1 : 0]) {
@@ -290,9 +304,14 @@ cudaError_t issue_sweep(ve_handle* h, int arith, bool warm) {
   if ((e = fft_forward(h->plan, h->X, h->specA, h->specB, h->tw, &spec, fp32, s)) != cudaSuccess)
     return e;
   if ((e = mark(5)) != cudaSuccess) return e;
-  if ((e = launch_xproj(h->plan, spec, h->canon, arith, h->vk[v], warm ? 1 : 0, s,
-                       h->prof ? h->jstats + 2 : nullptr, h->gws)) != cudaSuccess)
+  if (fp32 && h->tcmem) {
+    if ((e = launch_xproj_tc(h->plan, spec, h->canon, h->tcx, warm ? 1 : 0, s,
+                             h->prof ? h->jstats + 3 : nullptr)) != cudaSuccess)
+      return e;
+  } else if ((e = launch_xproj(h->plan, spec, h->canon, arith, h->vk[v], warm ? 1 : 0, s,
+                              h->prof ? h->jstats + 3 : nullptr, h->gws, &h->dst->iter)) != cudaSuccess) {
     return e;
+  }
   if ((e = mark(6)) != cudaSuccess) return e;
   if ((e = fft_inverse(h->plan, spec, h->specA, h->specB, h->X, h->tw, fp32, s)) != cudaSuccess)
     return e;
@@ -353,7 +372,10 @@ int run_sweeps(ve_handle* h, long count, int arith) {
 
 int read_status(ve_handle* h, ve_status* out) {
   VE_CU(cudaMemcpyAsync(h->hst, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+  int tc_err = 0;
+  if (h->tcmem) VE_CU(cudaMemcpyAsync(&tc_err, h->tcx.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   VE_CU(cudaStreamSynchronize(h->stream));
+  if (tc_err) return VE_ETIMEOUT;  // a tensor-core kernel gave up waiting: the sweep is invalid
   if (out) {
     out->iter = (long)h->hst->iter;
     out->energy_per_spin = h->hst->energy;
@@ -400,6 +422,7 @@ const char* ve_error_string(int code) {
     case VE_ECUDA: return "CUDA error";
     case VE_ENONFINITE: return "non-finite value in the iteration";
     case VE_EUNSUPPORTED: return "unsupported size";
+    case VE_ETIMEOUT: return "a device-side wait timed out";
     default: return "unknown status";
   }
 }
@@ -518,7 +541,7 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   const size_t o_sb = take(sizeof(double2) * N * h->plan.E);
   const size_t o_tw = take(sizeof(double2) * h->plan.ntw);
   const size_t o_st = take(sizeof(DevStatus));
-  const size_t o_js = take(sizeof(unsigned long long) * 4);
+  const size_t o_js = take(sizeof(unsigned long long) * 6);
   size_t gws_bytes = pair_ws_bytes(D);
   if (xproj_ws_bytes(D) > gws_bytes) gws_bytes = xproj_ws_bytes(D);
   if (bound_ws_bytes(D) > gws_bytes) gws_bytes = bound_ws_bytes(D);
@@ -571,6 +594,26 @@ int ve_create(const ve_lattice* lattice, const ve_cluster* cluster, const ve_ham
   h->dst = (DevStatus*)(base + o_st);
   h->jstats = (unsigned long long*)(base + o_js);
   h->gws = gws_bytes > 0 ? (unsigned char*)(base + o_gws) : nullptr;
+  if (D == 256 && h->opt.precision == VE_PREC_MIXED) {
+    // the pair work items are known only below; P bounds their number
+    const long nc = fft_ncanon(h->plan);
+    const size_t tx = tc_proj_ws_bytes(nc, 1), tp = tc_proj_ws_bytes(P, 0);
+    const size_t tr = (size_t)P * DD * sizeof(float);
+    if (cudaMalloc(&h->tcmem, tx + tp + tr) != cudaSuccess) {
+      cudaGetLastError();
+      h->tcmem = nullptr;
+      ve_destroy(h);
+      return VE_ENOMEM;
+    }
+    unsigned char* tb = (unsigned char*)h->tcmem;
+    if (tc_proj_ws_init(h->tcx, nc, 1, tb, tx) != 0 || tc_proj_ws_init(h->tcp, P, 0, tb + tx, tp) != 0 ||
+        cudaMemset(h->tcx.err, 0, sizeof(int)) != cudaSuccess) {
+      ve_destroy(h);
+      return VE_ECUDA;
+    }
+    h->tcp.err = h->tcx.err;  // one error word for both
+    h->rbuf = (float*)(tb + tx + tp);
+  }
   if (h->opt.stream) {
     h->stream = (cudaStream_t)h->opt.stream;
   } else {
@@ -652,6 +695,7 @@ void ve_destroy(ve_handle* h) {
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   if (h->hst) cudaFreeHost(h->hst);
   if (h->dev) cudaFree(h->dev);
+  if (h->tcmem) cudaFree(h->tcmem);
   delete h;
 }
 
@@ -703,7 +747,7 @@ int ve_profile(ve_handle* h, int enable) {
       h->prof_ms[i] = 0.0;
       h->prof_launch[i] = 0;
     }
-    VE_CU(cudaMemsetAsync(h->jstats, 0, sizeof(unsigned long long) * 4, h->stream));
+    VE_CU(cudaMemsetAsync(h->jstats, 0, sizeof(unsigned long long) * 6, h->stream));
     VE_CU(cudaStreamSynchronize(h->stream));
   }
   h->prof = enable != 0;
@@ -713,11 +757,24 @@ int ve_profile(ve_handle* h, int enable) {
 int ve_profile_sweeps(ve_handle* h, double* pair, double* wavevector) {
   if (!h || !pair || !wavevector) return VE_EINVAL;
   DeviceGuard g(h->device);
-  unsigned long long c[4] = {0, 0, 0, 0};
+  unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
   VE_CU(cudaMemcpyAsync(c, h->jstats, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
   VE_CU(cudaStreamSynchronize(h->stream));
   *pair = c[1] ? (double)c[0] / (double)c[1] : 0.0;
-  *wavevector = c[3] ? (double)c[2] / (double)c[3] : 0.0;
+  *wavevector = c[4] ? (double)c[3] / (double)c[4] : 0.0;
+  return VE_OK;
+}
+
+int ve_profile_first_order(ve_handle* h, long* pair, long* wavevector) {
+  if (!h || !pair || !wavevector) return VE_EINVAL;
+  DeviceGuard g(h->device);
+  unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
+  VE_CU(cudaMemcpyAsync(c, h->jstats, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+  VE_CU(cudaStreamSynchronize(h->stream));
+  pair[0] = (long)c[2];
+  pair[1] = (long)c[1];
+  wavevector[0] = (long)c[5];
+  wavevector[1] = (long)c[4];
   return VE_OK;
 }
 
@@ -836,7 +893,12 @@ int ve_bound(ve_handle* h, ve_cert* out) {
   double raw = (double)N * l0;
   for (int p = 0; p < P; ++p) raw += (double)md.count[p + 1] * lp[p];
   double xmin = INFINITY;
-  for (int k = 0; k < h->ncanon; ++k) xmin = lk[k] < xmin ? lk[k] : xmin;
+  bool finite = std::isfinite(raw);  // a NaN or Inf in any pair or cluster term reaches raw
+  for (int k = 0; k < h->ncanon; ++k) {
+    finite = finite && std::isfinite(lk[k]);
+    xmin = lk[k] < xmin ? lk[k] : xmin;
+  }
+  if (!finite) return VE_ENONFINITE;  // a non-finite state certifies nothing
   const double corr = (double)N * md.m * (xmin < 0 ? -xmin : 0.0);
   const double spins = (double)N * md.L;
   out->raw_bound = raw;

@@ -10,6 +10,9 @@
 //   K_0     = H'_0 - sum_delta Lambda1_delta.
 // This file computes lmin(K_delta) for every delta and lmin(K_0) in float64 (values-only
 // Jacobi); the host adds the weights c(delta) and the correction for a slightly indefinite X.
+// Each lmin is the smallest diagonal entry of the rotated matrix minus the Frobenius norm of its
+// remaining off-diagonal part, a lower bound by Weyl's inequality whether or not the Jacobi
+// sweeps converged; minima pass a NaN on (nan_min), so a non-finite state cannot certify.
 #include "ve_device.cuh"
 #include "ve_internal.h"
 
@@ -65,11 +68,13 @@ __global__ void __launch_bounds__(BShape<D>::NT * BShape<D>::GPC, GroupShape<D>:
       }
     }
     gsync<NT>();
-    jacobi_sym<double, D, LD, NT, false>(A, nullptr, cs, red, tid);
+    double off = 0.0;
+    jacobi_sym<double, D, LD, NT, false>(A, nullptr, cs, red, tid, nullptr, &off);
     double w = INFINITY;
-    for (int k = tid; k < D; k += NT) w = fmin(w, A[k * LD + k]);
+    for (int k = tid; k < D; k += NT) w = nan_min(w, A[k * LD + k]);
     w = gmin<NT>(w, red);
-    if (tid == 0) a.lmin_pairs[p] = w;
+    // Weyl: the rotated matrix is diag + E, so lmin >= min diag - ||E||_2 >= min diag - ||E||_F
+    if (tid == 0) a.lmin_pairs[p] = w - sqrt(off);
     gsync<NT>();
   }
 }
@@ -111,11 +116,12 @@ __global__ void __launch_bounds__(256) k_bound_k0(const BoundArgs a) {
       }
     }
     __syncwarp();
-    jacobi_sym<double, m, LD, 32, false>(A, nullptr, cs, red, t);
+    double off = 0.0;
+    jacobi_sym<double, m, LD, 32, false>(A, nullptr, cs, red, t, nullptr, &off);
     double w = INFINITY;
-    for (int k = t; k < m; k += 32) w = fmin(w, A[k * LD + k]);
+    for (int k = t; k < m; k += 32) w = nan_min(w, A[k * LD + k]);
     w = gmin<32>(w, red);
-    if (t == 0) a.lmin0[0] = w;
+    if (t == 0) a.lmin0[0] = w - sqrt(off);  // Weyl, as in k_bound_pairs
   }
 }
 

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(1024) k_dense_dk_check(const double* B, int n,
       const double a = 0.5 * (B[e] + B[(size_t)j * n + i]);
       off = fma(2.0 * a, a, off);
     } else if (i == j) {
-      d = fmin(d, fabs(B[e]));
+      d = nan_min(d, fabs(B[e]));
     }
   }
   off = gsum<1024>(off, red);
@@ -215,9 +215,31 @@ __global__ void __launch_bounds__(256) k_dense_rayleigh(const double* Vt, const 
 __global__ void __launch_bounds__(256) k_dense_min(const double* lam, int n, DenseCtl* ctl) {
   __shared__ double red[8];
   double v = INFINITY;
-  for (int k = threadIdx.x; k < n; k += 256) v = fmin(v, lam[k]);
+  for (int k = threadIdx.x; k < n; k += 256) v = nan_min(v, lam[k]);
   v = gmin<256>(v, red);
   if (threadIdx.x == 0) ctl->lmin = v;
+}
+
+// A certified lmin from the explicit A = V^T Y V = diag + E (B[i][j] = v_i.w_j, symmetrised):
+// by Weyl's inequality every eigenvalue of A lies within ||E||_2 <= ||E||_F of the sorted
+// diagonal, so lmin(Y) >= min_i a_ii - ||E||_F whether or not the sweeps converged.  A NaN
+// passes through to ctl->lmin.
+__global__ void __launch_bounds__(1024) k_dense_weyl_min(const double* B, int n, DenseCtl* ctl) {
+  __shared__ double red[32];
+  double off = 0.0, d = INFINITY;
+  const size_t nn = (size_t)n * n;
+  for (size_t e = threadIdx.x; e < nn; e += 1024) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i < j) {
+      const double a = 0.5 * (B[e] + B[(size_t)j * n + i]);
+      off = fma(2.0 * a, a, off);
+    } else if (i == j) {
+      d = nan_min(d, B[e]);
+    }
+  }
+  off = gsum<1024>(off, red);
+  d = gmin<1024>(d, red);
+  if (threadIdx.x == 0) ctl->lmin = d - sqrt(off);
 }
 
 // C (M x N) = op(A) diag(s) op(B), op(A)(i,k) = TA ? A[k][i] : A[i][k], op(B)(k,j) = TB ? B[j][k] :
@@ -481,6 +503,15 @@ cudaError_t dense_reconstruct(DenseWs& w, double* X, cudaStream_t s) {
 cudaError_t dense_lmin(DenseWs& w, cudaStream_t s) {
   k_dense_min<<<1, 256, 0, s>>>(w.lam, w.n, w.ctl);
   w.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t dense_lmin_certified(DenseWs& w, cudaStream_t s) {
+  const int n = w.n;
+  cudaError_t e = gemm<false, true>(n, n, n, w.Vt, n, w.Wt, n, w.Bt, n, nullptr, s);
+  if (e != cudaSuccess) return e;
+  k_dense_weyl_min<<<1, 1024, 0, s>>>(w.Bt, n, w.ctl);
+  w.launches += 2;
   return cudaGetLastError();
 }
 

@@ -61,5 +61,8 @@ cudaError_t dense_eig(DenseWs& w, const double* Y, int mode, cudaStream_t s);
 cudaError_t dense_reconstruct(DenseWs& w, double* X, cudaStream_t s);
 // ctl->lmin = min_i lambda_i after dense_eig.
 cudaError_t dense_lmin(DenseWs& w, cudaStream_t s);
+// ctl->lmin = min_i a_ii - ||offdiag(A)||_F for A = V^T Y V formed from Vt and Wt after
+// dense_eig: a lower bound on lmin(Y) by Weyl's inequality (one GEMM into Bt).
+cudaError_t dense_lmin_certified(DenseWs& w, cudaStream_t s);
 
 }  // namespace ve

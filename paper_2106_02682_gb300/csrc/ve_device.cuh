@@ -63,10 +63,18 @@ __device__ __forceinline__ T gsum(T v, T* red) {
   }
 }
 
+// min(a, b) that passes a NaN of either argument on (fmin drops it): a reduction that feeds a
+// certificate must not turn a non-finite input into a finite minimum.
+__device__ __forceinline__ double nan_min(double a, double b) { return (a < b || a != a) ? a : b; }
+__device__ __forceinline__ float nan_min(float a, float b) { return (a < b || a != a) ? a : b; }
+__device__ __forceinline__ df64 nan_min(df64 a, df64 b) {
+  return (a < b || a.hi != a.hi) ? a : b;
+}
+
 template <int NT, typename T>
 __device__ __forceinline__ T gmin(T v, T* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, shfl_xor(v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nan_min(v, shfl_xor(v, o));
   if constexpr (NT == 32) {
     return v;
   } else {
@@ -77,7 +85,7 @@ __device__ __forceinline__ T gmin(T v, T* red) {
     if (w == 0) {
       T s = red[lane < NT / 32 ? lane : 0];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s = fmin(s, shfl_xor(s, o));
+      for (int o = 16; o > 0; o >>= 1) s = nan_min(s, shfl_xor(s, o));
       __syncwarp();
       if (lane == 0) red[0] = s;
     }
@@ -331,7 +339,7 @@ __device__ __forceinline__ void unit_phase<df64>(df64 br, df64 bi, df64& mag, df
 template <typename T, int n, int LD, int NT>
 __device__ bool dk_stop(const T* A, T off, T nrm, T* red, int tid) {
   T d = T(1e30f);
-  for (int k = tid; k < n; k += NT) d = fmin(d, fabs(A[k * LD + k]));
+  for (int k = tid; k < n; k += NT) d = nan_min(d, fabs(A[k * LD + k]));
   d = gmin<NT>(d, red);
   return off * off <= T(JacobiStop<T, n>::rel2) * nrm * d * d && T(16) * off <= d * d;
 }
@@ -400,7 +408,8 @@ __device__ void dk_matrix_herm(T* Ar, T* Ai, T* lam, int tid) {
 // With DK the sweeps may also stop early under dk_stop; *dk then tells the caller to
 // reconstruct with the first-order correction (dk_matrix) instead of diag(max(l, 0)).
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
-__device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr) {
+__device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr,
+                          T* off_out = nullptr) {
   static_assert(n == 2 || n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   // blocks (GB) and eigenvector rows (GV) a thread loads before it stores any: a matrix staged
@@ -422,6 +431,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
   }
   gsync<NT>();
   if constexpr (DK) *dk = false;
+  T off_last = T(0);
   int sweep = 0;
   for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
     T off = T(0);
@@ -433,6 +443,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
       }
     }
     off = gsum<NT>(off, red);
+    off_last = off;
     if (off <= T(JacobiStop<T, n>::rel2) * nrm) break;
     if constexpr (DK) {
       if (dk_stop<T, n, LD, NT>(A, off, nrm, red, tid)) {
@@ -563,6 +574,17 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
       gsync<NT>();
     }
   }
+  if (off_out) {
+    if (sweep == JacobiTol<T>::max_sweeps) {  // the last sweep ran after the last test
+      T off = T(0);
+      for (int e = tid; e < n * n; e += NT) {
+        const int i = e / n, j = e % n;
+        if (i != j) off += A[i * LD + j] * A[i * LD + j];
+      }
+      off_last = gsum<NT>(off, red);
+    }
+    *off_out = off_last;
+  }
   return sweep;
 }
 
@@ -571,7 +593,8 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
 // diagonalises the 2x2 block; A <- U^H A U, V <- V U.  cs: shared scratch of 2n entries.
 // Returns the number of sweeps performed.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
-__device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, bool* dk = nullptr) {
+__device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, bool* dk = nullptr,
+                           T* off_out = nullptr) {
   static_assert(n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;  // as in jacobi_sym (measured)
@@ -591,6 +614,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, b
   }
   gsync<NT>();
   if constexpr (DK) *dk = false;
+  T off_last = T(0);
   int sweep = 0;
   for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
     T off = T(0);
@@ -602,6 +626,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, b
       }
     }
     off = gsum<NT>(off, red);
+    off_last = off;
     if (off <= T(JacobiStop<T, n>::rel2) * nrm) break;
     if constexpr (DK) {
       if (dk_stop<T, n, LD, NT>(Ar, off, nrm, red, tid)) {
@@ -791,6 +816,20 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, b
       }
       gsync<NT>();
     }
+  }
+  if (off_out) {
+    if (sweep == JacobiTol<T>::max_sweeps) {  // the last sweep ran after the last test
+      T off = T(0);
+      for (int e = tid; e < n * n; e += NT) {
+        const int i = e / n, j = e % n;
+        if (i != j) {
+          const int o = i * LD + j;
+          off += Ar[o] * Ar[o] + Ai[o] * Ai[o];
+        }
+      }
+      off_last = gsum<NT>(off, red);
+    }
+    *off_out = off_last;
   }
   return sweep;
 }

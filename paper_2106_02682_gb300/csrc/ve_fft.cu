@@ -65,6 +65,9 @@ __device__ __forceinline__ V cmul(V a, V b) {
 
 __device__ __forceinline__ int bitrev(int j, int logn) { return (int)(__brev((unsigned)j) >> (32 - logn)); }
 
+// tf32 part of a float32 value (the significand bits a tf32 tensor-core operand keeps).
+__device__ __forceinline__ float tc_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
 constexpr int FFT_EC = 32;        // largest number of entries per CTA
 constexpr int FFT_THREADS = 256;
 
@@ -227,7 +230,7 @@ template <int D, typename T>
 __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupShape<D>::MINB)
     k_xproj(typename C2<typename SpecOf<T>::R>::type* spec, const int* __restrict__ canon, const int ncanon,
             const FftPlan p, const double invN, T* vstore, const int warm,
-            unsigned long long* stats, unsigned char* gws) {
+            unsigned long long* stats, unsigned char* gws, const long long* iter) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
   constexpr int GPC = GroupShape<D>::GPC;
   using S = XSmem<D, T>;
@@ -258,8 +261,8 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
         Vi[(e / D) * LD + (e % D)] = vi[e];
       }
       gsync<NT>();
-      if constexpr (sizeof(T) == 4) {
-        // one Newton-Schulz step V <- V (3 I - V^H V) / 2 against float32 drift of the
+      if (ns_due<T>(iter)) {
+        // one Newton-Schulz step V <- V (3 I - V^H V) / 2 against the rounding drift of the
         // stored eigenvectors (Wr/Wi hold the Gram correction, Ar/Ai the new V)
         for (int e = tid; e < D * D; e += NT) {
           const int i = e / D, jj = e % D;
@@ -333,6 +336,7 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
     if (stats && tid == 0) {
       atomicAdd(stats, (unsigned long long)nsw);
       atomicAdd(stats + 1, 1ull);
+      if (dk) atomicAdd(stats + 2, 1ull);
     }
     if (vr) {
       for (int e = tid; e < D * D; e += NT) {
@@ -455,11 +459,13 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
     const int s = canon[j];
     const int s2 = partner_slot(p, s);
     unpack_block<D, NT, LD, double>(spec, s, s2, p.E, Ar, Ai, tid);
-    jacobi_herm<double, D, LD, NT, false>(Ar, Ai, nullptr, nullptr, cs, red, tid);
+    double off = 0.0;
+    jacobi_herm<double, D, LD, NT, false>(Ar, Ai, nullptr, nullptr, cs, red, tid, nullptr, &off);
     double w = INFINITY;
-    for (int k = tid; k < D; k += NT) w = fmin(w, Ar[k * LD + k]);
+    for (int k = tid; k < D; k += NT) w = nan_min(w, Ar[k * LD + k]);
     w = gmin<NT>(w, red);
-    if (tid == 0) lmin[j] = w;
+    // Weyl: lmin >= min diag - ||E||_F for the rotated diag + E; a NaN passes through
+    if (tid == 0) lmin[j] = w - sqrt(off);
     gsync<NT>();
   }
 }
@@ -468,7 +474,7 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
 template <int D, typename T>
 cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, void* vstore,
                            int warm, cudaStream_t s, unsigned long long* stats,
-                           unsigned char* gws) {
+                           unsigned char* gws, const long long* iter) {
   constexpr int NT = GroupShape<D>::NT, GPC = GroupShape<D>::GPC;
   constexpr bool G = GroupShape<D>::GLOBAL;
   const size_t smem = G ? 0 : XSmem<D, T>::bytes * GPC;
@@ -485,7 +491,7 @@ cudaError_t launch_xproj_t(const FftPlan& p, double2* spec, const int* canon, vo
   if (blocks > res) blocks = res;
   k_xproj<D, T><<<(unsigned)blocks, NT * GPC, smem, s>>>(
       reinterpret_cast<typename C2<typename SpecOf<T>::R>::type*>(spec), canon, nc, p, 1.0 / p.N,
-      reinterpret_cast<T*>(vstore), warm, stats, gws);
+      reinterpret_cast<T*>(vstore), warm, stats, gws, iter);
   return cudaGetLastError();
 }
 
@@ -795,28 +801,103 @@ cudaError_t fft_inverse(const FftPlan& p, double2* spec, double2* bufA, double2*
   return run_pass(p, p.inv[1], +1, nullptr, other, nullptr, x, tw, fp32, s);
 }
 
+// ---- D = 256 in float32: the projection itself runs in ve_tcproj.cu (tensor-core products);
+// these kernels move the canonical blocks between the float32 spectrum and its split KC4 input
+// and output buffers.
+__device__ __forceinline__ float2 x256_entry(const float2* spec, int s, int s2, int E, int f) {
+  if (f < E) {  // (z + conj(zz)) / 2
+    const float2 z = spec[(long)s * E + f], zz = spec[(long)s2 * E + f];
+    return make_float2(0.5f * (z.x + zz.x), 0.5f * (z.y - zz.y));
+  }
+  const float2 z = spec[(long)s * E + f - E], zz = spec[(long)s2 * E + f - E];  // (z - conj(zz)) / 2i
+  return make_float2(0.5f * (z.y + zz.y), -0.5f * (z.x - zz.x));
+}
+
+__global__ void __launch_bounds__(256) k_x256_unpack(const float2* __restrict__ spec, const int* __restrict__ canon,
+                                                     int ncanon, const FftPlan p, float* __restrict__ C) {
+  constexpr int D = 256, PL = D * D;
+  const long total = (long)ncanon * (PL / 4);
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(q / (PL / 4)), c4 = (int)(q % (PL / 4));
+    const int r = c4 % D, k0 = (c4 / D) * 4;
+    const int s = canon[j], s2 = partner_slot(p, s);
+    float re[4], im[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + u;
+      const float2 a = x256_entry(spec, s, s2, p.E, r * D + k);
+      const float2 b = x256_entry(spec, s, s2, p.E, k * D + r);
+      re[u] = r == k ? a.x : 0.5f * (a.x + b.x);  // Hermitised as in unpack_block
+      im[u] = r == k ? 0.f : 0.5f * (a.y - b.y);
+    }
+    float* out = C + (size_t)j * 4 * PL + 4 * (size_t)c4;
+    float4 h, l;
+    h = make_float4(tc_hi(re[0]), tc_hi(re[1]), tc_hi(re[2]), tc_hi(re[3]));
+    l = make_float4(re[0] - h.x, re[1] - h.y, re[2] - h.z, re[3] - h.w);
+    *reinterpret_cast<float4*>(out) = h;
+    *reinterpret_cast<float4*>(out + PL) = l;
+    h = make_float4(tc_hi(im[0]), tc_hi(im[1]), tc_hi(im[2]), tc_hi(im[3]));
+    l = make_float4(im[0] - h.x, im[1] - h.y, im[2] - h.z, im[3] - h.w);
+    *reinterpret_cast<float4*>(out + 2 * PL) = h;
+    *reinterpret_cast<float4*>(out + 3 * PL) = l;
+  }
+}
+
+// Y_k (split KC4, Hermitian) back into the spectrum, scaled by 1/N, with Y_{-k} = conj Y_k.
+__global__ void __launch_bounds__(256) k_x256_pack(const float* __restrict__ Y, const int* __restrict__ canon,
+                                                   int ncanon, const FftPlan p, float sc, float2* __restrict__ spec) {
+  constexpr int D = 256, PL = D * D;
+  const int E = p.E;
+  const long total = (long)ncanon * E;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(q / E), e = (int)(q % E);
+    const int s = canon[j], s2 = partner_slot(p, s);
+    const float* y = Y + (size_t)j * 4 * PL;
+    const int i1 = e / D, k1 = e % D, i2 = (e + E) / D, k2 = (e + E) % D;
+    const int o1 = ((k1 >> 2) * D + i1) * 4 + (k1 & 3), o2 = ((k2 >> 2) * D + i2) * 4 + (k2 & 3);
+    const float y1r = (y[o1] + y[PL + o1]) * sc, y1i = (y[2 * PL + o1] + y[3 * PL + o1]) * sc;
+    const float y2r = (y[o2] + y[PL + o2]) * sc, y2i = (y[2 * PL + o2] + y[3 * PL + o2]) * sc;
+    spec[(long)s * E + e] = make_float2(y1r - y2i, y1i + y2r);
+    if (s2 != s) spec[(long)s2 * E + e] = make_float2(y1r + y2i, y2r - y1i);
+  }
+}
+
 template <int D>
 cudaError_t launch_xproj_d(const FftPlan& p, double2* spec, const int* canon, int arith,
                            void* vstore, int warm, cudaStream_t s, unsigned long long* stats,
-                           unsigned char* gws) {
+                           unsigned char* gws, const long long* iter) {
   switch (arith) {
-    case ARITH_FP64: return launch_xproj_t<D, double>(p, spec, canon, vstore, warm, s, stats, gws);
-    case ARITH_FP32: return launch_xproj_t<D, float>(p, spec, canon, vstore, warm, s, stats, gws);
-    case ARITH_DF64: return launch_xproj_t<D, df64>(p, spec, canon, vstore, warm, s, stats, gws);
+    case ARITH_FP64: return launch_xproj_t<D, double>(p, spec, canon, vstore, warm, s, stats, gws, iter);
+    case ARITH_FP32: return launch_xproj_t<D, float>(p, spec, canon, vstore, warm, s, stats, gws, iter);
+    case ARITH_DF64: return launch_xproj_t<D, df64>(p, spec, canon, vstore, warm, s, stats, gws, iter);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, int arith,
                          void* vstore, int warm, cudaStream_t s, unsigned long long* stats,
-                         unsigned char* gws) {
+                         unsigned char* gws, const long long* iter) {
   switch (p.D) {
-    case 4: return launch_xproj_d<4>(p, spec, canon, arith, vstore, warm, s, stats, gws);
-    case 16: return launch_xproj_d<16>(p, spec, canon, arith, vstore, warm, s, stats, gws);
-    case 64: return launch_xproj_d<64>(p, spec, canon, arith, vstore, warm, s, stats, gws);
-    case 256: return launch_xproj_d<256>(p, spec, canon, arith, vstore, warm, s, stats, gws);
+    case 4: return launch_xproj_d<4>(p, spec, canon, arith, vstore, warm, s, stats, gws, iter);
+    case 16: return launch_xproj_d<16>(p, spec, canon, arith, vstore, warm, s, stats, gws, iter);
+    case 64: return launch_xproj_d<64>(p, spec, canon, arith, vstore, warm, s, stats, gws, iter);
+    case 256: return launch_xproj_d<256>(p, spec, canon, arith, vstore, warm, s, stats, gws, iter);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_xproj_tc(const FftPlan& p, double2* spec, const int* canon, TcProjWs& w, int warm,
+                            cudaStream_t s, unsigned long long* stats) {
+  if (p.D != 256 || !w.cplx) return cudaErrorInvalidValue;
+  const int nc = fft_ncanon(p);
+  float2* sp = reinterpret_cast<float2*>(spec);
+  const int grid = 4 * big_grid();
+  k_x256_unpack<<<grid, 256, 0, s>>>(sp, canon, nc, p, w.C);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = tc_project256(w, nc, warm != 0, stats, s)) != cudaSuccess) return e;
+  k_x256_pack<<<grid, 256, 0, s>>>(w.Wt, canon, nc, p, (float)(1.0 / p.N), sp);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon, double* lmin,

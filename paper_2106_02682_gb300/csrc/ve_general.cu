@@ -18,6 +18,8 @@
 // sign whose fixed point meets the optimality conditions (the paper prints X + eps G).
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdint.h>
 #include <string.h>
 
@@ -437,11 +439,13 @@ __global__ void __launch_bounds__(GroupShape<D>::NT, GroupShape<D>::MINB) k5_bou
       A[j * LD + i] = v;
     }
     gsync<NT>();
-    jacobi_sym<double, D, LD, NT, false>(A, nullptr, cs, red, tid);
+    double off = 0.0;
+    jacobi_sym<double, D, LD, NT, false>(A, nullptr, cs, red, tid, nullptr, &off);
     double v = INFINITY;
-    for (int k = tid; k < D; k += NT) v = fmin(v, A[k * LD + k]);
+    for (int k = tid; k < D; k += NT) v = nan_min(v, A[k * LD + k]);
     v = gmin<NT>(v, red);
-    if (tid == 0) lmin[p] = v;
+    // Weyl: lmin >= min diag - ||E||_F for the rotated diag + E; a NaN passes through
+    if (tid == 0) lmin[p] = v - sqrt(off);
     gsync<NT>();
   }
 }
@@ -477,11 +481,12 @@ __global__ void __launch_bounds__(32) k5_bound_cluster(const GenArgs a, double* 
     }
   }
   __syncwarp();
-  jacobi_sym<double, m, LD, 32, false>(A, nullptr, cs, red, t);
+  double off = 0.0;
+  jacobi_sym<double, m, LD, 32, false>(A, nullptr, cs, red, t, nullptr, &off);
   double v = INFINITY;
-  for (int k = t; k < m; k += 32) v = fmin(v, A[k * LD + k]);
+  for (int k = t; k < m; k += 32) v = nan_min(v, A[k * LD + k]);
   v = gmin<32>(v, red);
-  if (t == 0) lmin[i] = v;
+  if (t == 0) lmin[i] = v - sqrt(off);  // Weyl, as in k5_bound_pair
 }
 
 template <int D>
@@ -1128,7 +1133,7 @@ int ve_general_bound(ve_general* h, ve_cert* out) {
   const size_t nd = (size_t)h->n * h->n * sizeof(double);
   VG_CU(cudaMemcpyAsync(h->bws.Vt, h->dws.Vt, nd, cudaMemcpyDeviceToDevice, s));
   VG_CU(dense_eig(h->bws, h->X, h->projections > 0 ? DENSE_WARM : DENSE_COLD, s));
-  VG_CU(dense_lmin(h->bws, s));
+  VG_CU(dense_lmin_certified(h->bws, s));
   std::vector<double> lp((size_t)h->K), lc((size_t)h->N);
   DenseCtl ctl;
   VG_CU(cudaMemcpyAsync(lp.data(), h->lmin_p, lp.size() * 8, cudaMemcpyDeviceToHost, s));
@@ -1136,11 +1141,13 @@ int ve_general_bound(ve_general* h, ve_cert* out) {
   VG_CU(cudaMemcpyAsync(&ctl, h->bws.ctl, sizeof(DenseCtl), cudaMemcpyDeviceToHost, s));
   ve_status st;
   const int r = read_status(h, &st);  // synchronises
-  if (r != VE_OK && r != VE_ENONFINITE) return r;
+  if (r != VE_OK) return r;  // a non-finite iterate certifies nothing
   double raw = 0.0;
   for (double v : lc) raw += v;
   for (double v : lp) raw += v;
   const double xmin = ctl.lmin;
+  // every minimum passes a NaN on, and an Inf stays in the sum: one check covers them all
+  if (!std::isfinite(raw) || !std::isfinite(xmin)) return VE_ENONFINITE;
   const double corr = (double)h->N * h->m * (xmin < 0 ? -xmin : 0.0);
   out->raw_bound = raw;
   out->x_min_eig = xmin;

@@ -26,6 +26,18 @@ inline cudaError_t smem_once(K kernel, size_t bytes, unsigned long long& mask) {
 }
 
 // ------------------------------------------------------------------ sweep kernels
+// Warm-started eigensolves rotate the eigenvectors kept from the previous sweep, and rounding
+// erodes their orthogonality a little every sweep; a drifted V makes V^T C V a non-similarity
+// and the projection inexact by as much.  A Newton-Schulz step V <- V (3 I - V^T V) / 2 squares
+// the drift: every sweep in float32, every NS_EVERY-th sweep in float64 and double-float words
+// (measured: the float64 state after 300 sweeps then agrees with the oracle to ~3e-13 instead of
+// ~1e-10 at D = 64, 256).
+constexpr int NS_EVERY = 8;
+template <typename T>
+__device__ __forceinline__ bool ns_due(const long long* iter) {
+  if (sizeof(T) == 4) return true;
+  return iter && (*iter % NS_EVERY) == 0;
+}
 struct PairArgs {
   int N, P, m, D;
   double mu, nu, eps;
@@ -42,7 +54,11 @@ struct PairArgs {
   double* part;         // P*2     ||rho - rho~||^2, Tr[H rho]
   void* vstore;         // P*D*D eigenvectors of the last projection (float or double)
   int warm;             // 1: start each Jacobi from V^T C V with the stored V
-  unsigned long long* stats;  // null, or [0] += Jacobi sweeps, [1] += matrices (profiling)
+  // sweeps done so far (device); the stored V is re-orthogonalised when it is a multiple of
+  // NS_EVERY (float64 / double-float; float32 every sweep).  null: never in those arithmetics
+  const long long* iter = nullptr;
+  // null, or [0] += Jacobi sweeps, [1] += matrices, [2] += first-order stops (profiling)
+  unsigned long long* stats;
   unsigned char* gws;   // D = 256: per-CTA staging workspace (pair_ws_bytes), else unused
   // Offsets delta and -delta carry swap images of each other; the pass runs over Pc items, item
   // i updating pair index pidx[i] (delta - 1) and writing the image into pmir[i] (-1: -delta =
@@ -50,6 +66,10 @@ struct PairArgs {
   int Pc;
   const int* pidx;
   const int* pmir;
+  // D = 256 in float32 with the projection on the tensor cores (null: the k_pair kernel):
+  // tcw holds the projection workspace for Pc matrices, rbuf Pc * D * D floats of rho
+  struct TcProjWs* tcw = nullptr;
+  float* rbuf = nullptr;
 };
 
 struct DevStatus {
@@ -142,10 +162,52 @@ int fft_ncanon(const FftPlan& p);
 // slot; warm = 1 starts from them.
 cudaError_t launch_xproj(const FftPlan& p, double2* spec, const int* canon, int arith,
                          void* vstore, int warm, cudaStream_t s,
-                         unsigned long long* stats = nullptr, unsigned char* gws = nullptr);
+                         unsigned long long* stats = nullptr, unsigned char* gws = nullptr,
+                         const long long* iter = nullptr);
+// D = 256 in float32 (float2 spectrum): the same projection with its products on the tensor
+// cores (tc_project256); the eigenvectors persist in w between calls.
+struct TcProjWs;
+cudaError_t launch_xproj_tc(const FftPlan& p, double2* spec, const int* canon, TcProjWs& w, int warm,
+                            cudaStream_t s, unsigned long long* stats = nullptr);
 // lmin[slot] = smallest eigenvalue of the (unnormalised) block C_k, +inf for non-canonical slots.
 cudaError_t launch_xeig(const FftPlan& p, const double2* spec, const int* canon, double* lmin,
                        cudaStream_t s, unsigned char* gws = nullptr);
+
+// ------------------------------------------------------------------ tensor-core products
+// Batched 256 x 256 x 256 products D_b = alpha x_b y_b^T + beta I on the tcgen05 tensor cores
+// (ve_tcgemm.cu): x and y are split float32 matrices in the KC4 layout -- per matrix 2 planes
+// (hi, lo) when real, 4 (re hi, re lo, im hi, im lo) when complex, each 256 x 256 with element
+// (r, k) at ((k / 4) * 256 + r) * 4 + k % 4 -- and x_b y_b^T contracts the k index of both.
+// conj_x / conj_y conjugate a complex operand.  The result goes to out_n (D, KC4, split) and/or
+// out_t (D^T); every pointer 16-byte aligned.  *err is set to 1 when a wait of the kernel gave up.
+struct TcGemm {
+  const float* x = nullptr;
+  const float* y = nullptr;
+  long batch = 0;
+  int cplx = 0, conj_x = 0, conj_y = 0;
+  float alpha = 1.f, beta = 0.f;
+  float* out_n = nullptr;
+  float* out_t = nullptr;
+  int* err = nullptr;
+};
+cudaError_t tc_gemm256(const TcGemm& g, cudaStream_t s);
+
+// Batched float32 PSD projection of 256 x 256 matrices with the products on the tensor cores
+// (ve_tcproj.cu).  One workspace serves up to `cap` matrices of one kind (real or complex); V and
+// Vt keep the eigenvectors between calls (warm = true starts from them, false from V = I).  The
+// caller writes the inputs C (split, KC4, symmetric / Hermitian) into w.C; the projections come
+// back in w.Wt (split, KC4).  stats as in PairArgs.
+struct TcProjWs {
+  long cap = 0;
+  int cplx = 0;
+  float *V = nullptr, *Vt = nullptr, *C = nullptr, *T = nullptr, *V1 = nullptr, *V1t = nullptr,
+        *Wt = nullptr, *M = nullptr, *Qt = nullptr;
+  unsigned char* jws = nullptr;  // Jacobi staging, one slice per CTA
+  int* err = nullptr;            // device word: 1 after a tensor-core kernel gave up waiting
+};
+size_t tc_proj_ws_bytes(long cap, int cplx);
+int tc_proj_ws_init(TcProjWs& w, long cap, int cplx, void* mem, size_t bytes);
+cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long* stats, cudaStream_t s);
 
 // ------------------------------------------------------------------ bound
 struct BoundArgs {

@@ -4,8 +4,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "../../include/ve.h"
 #include "ve_internal.h"
 
@@ -17,25 +15,16 @@ namespace {
 // its device address must come from cudaGetSymbolAddress on the device that runs the kernels.
 static __device__ __align__(256) unsigned char g_scratch[VE_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_address[kMaxDevices] = {};
-
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Device address of g_scratch on the current device, looked up once per device.
+// Device address of g_scratch on the current device, looked up on every call: the lookup is a
+// host-side query, and an address kept from an earlier call would go stale if the device's
+// primary context were torn down (cudaDeviceReset) and the module loaded again elsewhere.
 int scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return VE_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return VE_EUNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_address[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return VE_ECUDA;
-    g_address[dev] = p;
-  }
-  *out = g_address[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return VE_ECUDA;
+  *out = p;
   return VE_OK;
 }
 

@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
     if (a.warm) {
       for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = vs[e];
       gsync<NT>();
-      if constexpr (sizeof(T) == 4) {
-        // float32 rotations erode V's orthogonality over many sweeps; one Newton-Schulz step
+      if (ns_due<T>(a.iter)) {
+        // rotations erode V's orthogonality over many sweeps; one Newton-Schulz step
         // V <- V (3 I - V^T V) / 2 squares the error before V is used (A and Wt as scratch)
         for (int e = tid; e < D * D; e += NT) {
           const int i = e / D, j = e % D;
@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
     if (a.stats && tid == 0) {
       atomicAdd(a.stats, (unsigned long long)nsw);
       atomicAdd(a.stats + 1, 1ull);
+      if (dk) atomicAdd(a.stats + 2, 1ull);
     }
     for (int e = tid; e < D * D; e += NT) vs[e] = V[(e / D) * LD + (e % D)];
     if (dk) {
@@ -295,6 +296,181 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
     }
     gsync<NT>();
   }
+}
+
+// ---- D = 256 in float32 with the projection on the tensor cores (ve_tcproj.cu): the pair
+// pass splits around one batched projection.  k_pair256_pre forms rho (Eq. (rhoijUpdate)) into
+// rbuf and C = rho - Lambda / mu (symmetrised) into the projection's split input; after
+// tc_project256, k_pair256_post does what k_pair does after its eigensolve.  Arithmetic in
+// float32, as k_pair<256, float>.
+constexpr int P256_NT = 512;
+
+__device__ __forceinline__ float tf32_part(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__global__ void __launch_bounds__(P256_NT) k_pair256_pre(const PairArgs a, float* __restrict__ Cout) {
+  constexpr int D = 256, m = 16, NT = P256_NT, PL = D * D;
+  __shared__ float t1[m * m], t2[m * m];
+  __shared__ float rho0[m * m];
+  const int tid = threadIdx.x;
+  const float mu = (float)a.mu, nu = (float)a.nu;
+  const float alpha = nu * m;
+  const float c0 = 1.f / mu, c1 = 1.f / (mu + alpha), c2 = 1.f / (mu + 2.f * alpha);
+  const float imu = 1.f / mu;
+  for (int k = tid; k < m * m; k += NT) rho0[k] = (float)a.rho0[k];
+  for (long it = blockIdx.x; it < a.Pc; it += gridDim.x) {
+    const long p = a.pidx ? a.pidx[it] : it;
+    const long pm = a.pidx ? a.pmir[it] : -1;
+    const long dl = p + 1;
+    const double* rt = a.rt + p * PL;
+    const double* lam = a.lam + p * PL;
+    const double* l1 = a.lam1 + p * m * m;
+    const double* l2 = a.lam2 + p * m * m;
+    const double* Xb = a.X + dl * PL;
+    const int hs = a.hslot[dl];
+    const double* Hb = hs >= 0 ? a.hb + (long)hs * PL : nullptr;
+    float* R = a.rbuf + it * PL;
+    if (pm >= 0) {
+      for (int idx = tid; idx < m * m; idx += NT) {
+        a.lam1[pm * m * m + idx] = l2[idx];
+        a.lam2[pm * m * m + idx] = l1[idx];
+      }
+    }
+    __syncthreads();
+    // right-hand side of Eq. (rhoijUpdate) with H' of Eq. (effHam)
+    for (int e = tid; e < PL; e += NT) {
+      const int i = e / D, j = e % D;
+      const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+      const float h = Hb ? (float)Hb[e] : 0.f;
+      const float hp = h - (float)Xb[(pa * m + pc) * D + (pd * m + pb)] - (float)Xb[(pc * m + pa) * D + (pb * m + pd)];
+      float y = mu * (float)rt[e] + (float)lam[e] - hp;
+      if (pb == pd) y += nu * rho0[pa * m + pc] - (float)l1[pa * m + pc];
+      if (pa == pc) y += nu * rho0[pb * m + pd] - (float)l2[pb * m + pd];
+      R[e] = y;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += NT) {
+      const int x = idx / m, z = idx % m;
+      float s1 = 0.f, s2 = 0.f;
+      for (int k = 0; k < m; ++k) {
+        s1 += R[(x * m + k) * D + (z * m + k)];
+        s2 += R[(k * m + x) * D + (k * m + z)];
+      }
+      t1[idx] = s1;
+      t2[idx] = s2;
+    }
+    __syncthreads();
+    float tr = 0.f;
+    for (int k = 0; k < m; ++k) tr += t1[k * m + k];
+    for (int e = tid; e < PL; e += NT) {
+      const int i = e / D, j = e % D;
+      const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+      const float y = R[e];
+      const float P1 = (pb == pd) ? t1[pa * m + pc] / m : 0.f;
+      const float P2 = (pa == pc) ? t2[pb * m + pd] / m : 0.f;
+      const float Q = (i == j) ? tr / D : 0.f;
+      R[e] = (y - P1 - P2 + Q) * c0 + (P1 + P2 - 2.f * Q) * c1 + Q * c2;
+    }
+    __syncthreads();
+    // C = rho - Lambda / mu, symmetrised, split into the KC4 input of the projection
+    float* C = Cout + it * 2 * PL;
+    for (int q = tid; q < PL / 4; q += NT) {
+      const int r = q % D, k0 = (q / D) * 4;
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = k0 + u;
+        v[u] = 0.5f * (R[r * D + j] + R[j * D + r]) - 0.5f * ((float)lam[r * D + j] + (float)lam[j * D + r]) * imu;
+      }
+      float4 hi, lo;
+      hi = make_float4(tf32_part(v[0]), tf32_part(v[1]), tf32_part(v[2]), tf32_part(v[3]));
+      lo = make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
+      *reinterpret_cast<float4*>(C + 4 * q) = hi;
+      *reinterpret_cast<float4*>(C + PL + 4 * q) = lo;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(P256_NT) k_pair256_post(const PairArgs a, const float* __restrict__ Y) {
+  constexpr int D = 256, m = 16, NT = P256_NT, PL = D * D;
+  __shared__ float red[NT / 32];
+  const int tid = threadIdx.x;
+  const float mu = (float)a.mu, eps = (float)a.eps;
+  for (long it = blockIdx.x; it < a.Pc; it += gridDim.x) {
+    const long p = a.pidx ? a.pidx[it] : it;
+    const long pm = a.pidx ? a.pmir[it] : -1;
+    const long dl = p + 1;
+    const float* R = a.rbuf + it * PL;
+    const float* y = Y + it * 2 * PL;
+    double* Xb = a.X + dl * PL;
+    const int hs = a.hslot[dl];
+    const double* Hb = hs >= 0 ? a.hb + (long)hs * PL : nullptr;
+    double* rtw = a.rt + p * PL;
+    double* lamw = a.lam + p * PL;
+    double* rtm = pm >= 0 ? a.rt + pm * PL : nullptr;
+    double* lamm = pm >= 0 ? a.lam + pm * PL : nullptr;
+    double* Xm = pm >= 0 ? a.X + (pm + 1) * PL : nullptr;
+    float rr = 0.f, en = 0.f;
+    // X' reads X_{0,delta} before this item overwrites it: each thread rewrites only entries
+    // it has read (e), and the transposed image goes to another block (-delta)
+    for (int e = tid; e < PL; e += NT) {
+      const int i = e / D, j = e % D;
+      const int pa = i / m, pb = i % m, pc = j / m, pd = j % m;
+      const float rho = R[e];
+      const int o = ((j >> 2) * D + i) * 4 + (j & 3);
+      const float rtn = y[o] + y[PL + o];
+      const float h = Hb ? (float)Hb[e] : 0.f;
+      const double lamn = (double)((float)a.lam[p * PL + e] + mu * (rtn - rho));
+      const double xn = (double)((float)Xb[e] - eps * R[(pa * m + pd) * D + (pb * m + pc)]);
+      lamw[e] = lamn;
+      rtw[e] = (double)rtn;
+      Xb[e] = xn;
+      if (pm >= 0) {
+        const int es = (pb * m + pa) * D + (pd * m + pc);
+        lamm[es] = lamn;
+        rtm[es] = (double)rtn;
+        Xm[j * D + i] = xn;
+      }
+      rr += (rho - rtn) * (rho - rtn);
+      en += h * R[j * D + i];
+    }
+    for (int idx = tid; idx < m * m; idx += NT) {
+      const int x = idx / m, z = idx % m;
+      float s1 = 0.f, s2 = 0.f;
+      for (int k = 0; k < m; ++k) {
+        s1 += R[(x * m + k) * D + (z * m + k)];
+        s2 += R[(k * m + x) * D + (k * m + z)];
+      }
+      a.a1r[p * m * m + idx] = (double)s1;
+      a.a2r[p * m * m + idx] = (double)s2;
+      if (pm >= 0) {
+        a.a1r[pm * m * m + idx] = (double)s2;
+        a.a2r[pm * m * m + idx] = (double)s1;
+      }
+    }
+    rr = gsum<NT>(rr, red);
+    en = gsum<NT>(en, red);
+    if (tid == 0) {
+      a.part[p * 2 + 0] = (double)rr;
+      a.part[p * 2 + 1] = (double)en;
+      if (pm >= 0) {
+        a.part[pm * 2 + 0] = (double)rr;
+        a.part[pm * 2 + 1] = (double)en;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_pair_tc(const PairArgs& a, cudaStream_t s) {
+  TcProjWs& w = *a.tcw;
+  const int grid = (int)(a.Pc < 2 * big_grid() ? a.Pc : 2 * big_grid());
+  k_pair256_pre<<<grid, P256_NT, 0, s>>>(a, w.C);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = tc_project256(w, a.Pc, a.warm != 0, a.stats, s)) != cudaSuccess) return e;
+  k_pair256_post<<<grid, P256_NT, 0, s>>>(a, w.Wt);
+  return cudaGetLastError();
 }
 
 template <int D, typename T>
@@ -509,6 +685,7 @@ cudaError_t launch_pair_d(const PairArgs& a, int arith, cudaStream_t s) {
 }
 
 cudaError_t launch_pair(const PairArgs& a, int arith, cudaStream_t s) {
+  if (a.D == 256 && arith == ARITH_FP32 && a.tcw && a.rbuf) return launch_pair_tc(a, s);
   switch (a.D) {
     case 4: return launch_pair_d<4>(a, arith, s);
     case 16: return launch_pair_d<16>(a, arith, s);

@@ -1,0 +1,361 @@
+// ve_tcgemm.cu -- batched 256 x 256 x 256 products on the fifth-generation tensor cores, the
+// GEMM-shaped part of the float32 PSD projections of 256 x 256 marginals (Eq. (rhoijTildeUpdate)
+// and the per-wavevector step of Algorithm 6 of Khoo & Lindsey, arXiv:2106.02682): forming
+// V^H C V from the previous eigenvectors, updating them, and the reconstruction V M V^H.
+//
+// Operands are "split" float32 matrices: each real plane p of a matrix is stored as two planes,
+// hi = p rounded down to tf32 (the 10 significand bits the tensor core reads) and lo = p - hi
+// (exact), and a product P Q^T is taken as Phi Qhi^T + Phi Qlo^T + Plo Qhi^T in kind::tf32 MMAs
+// with float32 accumulation in tensor memory -- float32-level accuracy (~2^-21 relative per
+// product term) at the tf32 rate.  Complex matrices carry planes (re hi, re lo, im hi, im lo).
+//
+// Storage of one 256 x 256 plane, "KC4": element (r, k) at ((k / 4) * 256 + r) * 4 + k % 4 --
+// every 4 consecutive k of a row form one 16-byte chunk, and the chunks of consecutive rows are
+// adjacent.  A TMA box of 4 x R x 4 over (k % 4, r, k / 4) then lands in shared memory exactly in
+// the tensor core's no-swizzle K-major layout (8-row x 16-byte core matrices, 128 contiguous
+// bytes each), and a thread reading one row's chunk as a float4 is coalesced with its
+// neighbours.
+//
+// Kernel: one CTA per SM, persistent over (matrix, half) tiles of 128 x 256 outputs.  Warp 0
+// issues the TMA loads of 16-wide K slices into a ring of stages, warp 1 allocates tensor memory
+// and issues the MMAs from one thread, warps 2-5 read the accumulators back (tcgen05.ld) and
+// write the split result, normal and/or transposed.  Every wait is bounded (ve_tc.cuh).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "ve_internal.h"
+#include "ve_tc.cuh"
+
+namespace ve {
+
+namespace {
+
+using namespace tc;
+
+template <bool CPLX>
+struct TcCfg {
+  static constexpr int NPL = CPLX ? 4 : 2;            // planes of a split matrix
+  static constexpr int KS = 16;                       // K elements per stage
+  static constexpr int STAGES = CPLX ? 2 : 4;
+  static constexpr int XB = 128 * KS * 4;             // bytes of one X plane slice (128 rows)
+  static constexpr int YB = 256 * KS * 4;             // bytes of one Y plane slice (256 rows)
+  static constexpr int STAGE_BYTES = NPL * (XB + YB);
+  static constexpr int TMEM_COLS = CPLX ? 512 : 256;  // re and im accumulators, 256 columns each
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2048;  // + alignment, barriers
+};
+
+constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kPlane = 256 * 256;
+
+struct TcParams {
+  long batch;
+  int conj_x, conj_y;
+  float alpha, beta;
+  float* out_n;
+  float* out_t;
+  int* err;
+};
+
+// Element (r, k) of a KC4 plane.
+__device__ __forceinline__ int kc4(int r, int k) { return ((k >> 2) * 256 + r) * 4 + (k & 3); }
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tcgemm(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap my, const TcParams p) {
+  using C = TcCfg<CPLX>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* tfull = empty + C::STAGES;
+  uint64_t* tempty = tfull + 1;
+  uint64_t* drain = tempty + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long ntiles = 2 * p.batch;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 4);  // one arrival per epilogue warp
+    mbar_init(drain, 1);
+    *abort = 0;
+    fence_barrier_init();
+    prefetch_tensormap(&mx);
+    prefetch_tensormap(&my);
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued = 0, iph = 0;  // per stage: a load was issued, and the phase it completes
+      for (long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+        const int b = (int)(t >> 1), h = (int)(t & 1);
+        for (int kb = 0; kb < 256 / C::KS; ++kb) {
+          if (!mbar_wait(&empty[s], ph ^ 1, abort)) break;
+          issued |= 1u << s;
+          iph = (iph & ~(1u << s)) | (ph << s);
+          mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+          unsigned char* st = base + s * C::STAGE_BYTES;
+          for (int pl = 0; pl < C::NPL; ++pl) {
+            tma_load_4d(st + pl * C::XB, &mx, &full[s], 0, 128 * h, kb * (C::KS / 4), b * C::NPL + pl);
+            tma_load_4d(st + C::NPL * C::XB + pl * C::YB, &my, &full[s], 0, 0, kb * (C::KS / 4),
+                        b * C::NPL + pl);
+          }
+          if (++s == C::STAGES) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      if (*abort) {
+        // copies still in flight land before the CTA leaves: wait (bounded) for the phase each
+        // issued stage completes; a completed one returns at once
+        volatile int never = 0;
+        for (int k = 0; k < C::STAGES; ++k)
+          if (issued & (1u << k)) mbar_wait(&full[k], (iph >> k) & 1u, &never);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t XLBO = 128 * 16, YLBO = 256 * 16, SBO = 128;
+      // products of one K step: (x plane, y plane, accumulator column, negate)
+      // real: hi hi, hi lo, lo hi.  Complex x = xr + i sx xi, y = yr + i sy yi (s = -1 when
+      // conjugated): Dr = xr yr^T - sx sy xi yi^T, Di = sy xr yi^T + sx xi yr^T.
+      const int sx = p.conj_x ? -1 : 1, sy = p.conj_y ? -1 : 1;
+      int s = 0;
+      uint32_t ph = 0;
+      int local = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++local) {
+        if (!mbar_wait(tempty, (local & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        bool ok = true;
+        for (int kb = 0; kb < 256 / C::KS; ++kb) {
+          if (!mbar_wait(&full[s], ph, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(base + s * C::STAGE_BYTES);
+          const uint32_t xs = st, ys = st + C::NPL * C::XB;
+#pragma unroll
+          for (int ks = 0; ks < C::KS / 8; ++ks) {
+            auto mma = [&](int xp, int yp, uint32_t col, int neg, bool first) {
+              const uint64_t ad = smem_desc(xs + xp * C::XB + ks * 2 * XLBO, XLBO, SBO);
+              const uint64_t bd = smem_desc(ys + yp * C::YB + ks * 2 * YLBO, YLBO, SBO);
+              mma_tf32(tmem + col, ad, bd, idesc_tf32(128, 256, neg, 0), first ? 0u : 1u);
+            };
+            const bool f0 = kb == 0 && ks == 0;
+            if constexpr (!CPLX) {
+              mma(0, 0, 0, 0, f0);
+              mma(0, 1, 0, 0, false);
+              mma(1, 0, 0, 0, false);
+            } else {
+              const int nr = (sx * sy > 0) ? 1 : 0;  // Dr: - sx sy xi yi^T
+              mma(0, 0, 0, 0, f0);
+              mma(0, 1, 0, 0, false);
+              mma(1, 0, 0, 0, false);
+              mma(2, 2, 0, nr, false);
+              mma(2, 3, 0, nr, false);
+              mma(3, 2, 0, nr, false);
+              const int ni1 = sy < 0 ? 1 : 0, ni2 = sx < 0 ? 1 : 0;
+              mma(0, 2, 256, ni1, f0);
+              mma(0, 3, 256, ni1, false);
+              mma(1, 2, 256, ni1, false);
+              mma(2, 0, 256, ni2, false);
+              mma(2, 1, 256, ni2, false);
+              mma(3, 0, 256, ni2, false);
+            }
+          }
+          mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+          if (++s == C::STAGES) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+        if (!ok) break;
+        mma_commit(tfull);
+      }
+      if (*abort) {
+        // every MMA issued so far completes before this commit's arrival
+        mma_commit(drain);
+        volatile int never = 0;
+        mbar_wait(drain, 0, &never);
+      }
+    }
+  } else {
+    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) ... + 31, i.e. output rows
+    const int q = warp & 3;
+    const int m = 32 * q + lane;
+    int local = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+      const int b = (int)(t >> 1), h = (int)(t & 1);
+      // warp-uniform decision: the tensor-memory loads below are .sync.aligned
+      const bool ok = !*abort && mbar_wait(tfull, local & 1, abort);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int gr = 128 * h + m;  // output row
+      float* on = p.out_n ? p.out_n + (size_t)b * C::NPL * kPlane : nullptr;
+      float* ot = p.out_t ? p.out_t + (size_t)b * C::NPL * kPlane : nullptr;
+      for (int n0 = 0; n0 < 256; n0 += 16) {
+        float vr[16], vi[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + n0, vr);
+        if constexpr (CPLX) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 256 + n0, vi);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          vr[j] = p.alpha * vr[j] + ((gr == n0 + j) ? p.beta : 0.f);
+          if constexpr (CPLX) vi[j] = p.alpha * vi[j];
+        }
+        if (on) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int off = ((n0 / 4 + c) * 256 + gr) * 4;
+            float4 hi, lo;
+            hi.x = tf32_hi(vr[4 * c]);
+            hi.y = tf32_hi(vr[4 * c + 1]);
+            hi.z = tf32_hi(vr[4 * c + 2]);
+            hi.w = tf32_hi(vr[4 * c + 3]);
+            lo.x = vr[4 * c] - hi.x;
+            lo.y = vr[4 * c + 1] - hi.y;
+            lo.z = vr[4 * c + 2] - hi.z;
+            lo.w = vr[4 * c + 3] - hi.w;
+            *reinterpret_cast<float4*>(on + off) = hi;
+            *reinterpret_cast<float4*>(on + kPlane + off) = lo;
+            if constexpr (CPLX) {
+              hi.x = tf32_hi(vi[4 * c]);
+              hi.y = tf32_hi(vi[4 * c + 1]);
+              hi.z = tf32_hi(vi[4 * c + 2]);
+              hi.w = tf32_hi(vi[4 * c + 3]);
+              lo.x = vi[4 * c] - hi.x;
+              lo.y = vi[4 * c + 1] - hi.y;
+              lo.z = vi[4 * c + 2] - hi.z;
+              lo.w = vi[4 * c + 3] - hi.w;
+              *reinterpret_cast<float4*>(on + 2 * kPlane + off) = hi;
+              *reinterpret_cast<float4*>(on + 3 * kPlane + off) = lo;
+            }
+          }
+        }
+        if (ot) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int off = kc4(n0 + j, gr);
+            const float hr = tf32_hi(vr[j]);
+            ot[off] = hr;
+            ot[kPlane + off] = vr[j] - hr;
+            if constexpr (CPLX) {
+              const float hi2 = tf32_hi(vi[j]);
+              ot[2 * kPlane + off] = hi2;
+              ot[3 * kPlane + off] = vi[j] - hi2;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+  }
+
+  // ---- exit (the producer and the MMA thread have drained their work after an abort)
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort && p.err) atomicExch(p.err, 1);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// Tensor map over `planes` KC4 planes at `ptr`: dims (k % 4, r, k / 4, plane), box (4, rows, 4, 1).
+bool make_map(CUtensorMap* map, const float* ptr, long planes, int rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {4, 256, 64, (cuuint64_t)planes};
+  cuuint64_t strides[3] = {16, 256 * 16, (cuuint64_t)kPlane * 4};
+  cuuint32_t box[4] = {4, (cuuint32_t)rows, 4, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return n;
+}
+
+template <bool CPLX>
+cudaError_t launch(const TcGemm& g, cudaStream_t s) {
+  using C = TcCfg<CPLX>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tcgemm<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap mx, my;
+  if (!make_map(&mx, g.x, g.batch * C::NPL, 128) || !make_map(&my, g.y, g.batch * C::NPL, 256))
+    return cudaErrorInvalidValue;
+  TcParams p;
+  p.batch = g.batch;
+  p.conj_x = g.conj_x;
+  p.conj_y = g.conj_y;
+  p.alpha = g.alpha;
+  p.beta = g.beta;
+  p.out_n = g.out_n;
+  p.out_t = g.out_t;
+  p.err = g.err;
+  const long tiles = 2 * g.batch;
+  const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
+  k_tcgemm<CPLX><<<grid, kThreads, C::SMEM, s>>>(mx, my, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_gemm256(const TcGemm& g, cudaStream_t s) {
+  if (g.batch <= 0) return cudaSuccess;
+  if (!g.x || !g.y || (!g.out_n && !g.out_t)) return cudaErrorInvalidValue;
+  if (((uintptr_t)g.x | (uintptr_t)g.y | (uintptr_t)g.out_n | (uintptr_t)g.out_t) & 15)
+    return cudaErrorInvalidValue;
+  return g.cplx ? launch<true>(g, s) : launch<false>(g, s);
+}
+
+}  // namespace ve

@@ -1,0 +1,257 @@
+// ve_tcproj.cu -- batched float32 PSD projection of 256 x 256 matrices, Pi_{>=0}(C) = V max(L, 0)
+// V^H, with its GEMM-shaped work on the tensor cores (ve_tcgemm.cu).  It serves the float32
+// phase of the 4-spin-cluster solver: the pair projections of Eq. (rhoijTildeUpdate) (real
+// symmetric) and the per-wavevector projections of Algorithm 6 (complex Hermitian), Khoo &
+// Lindsey, arXiv:2106.02682.
+//
+// Per matrix, starting from the eigenvectors V kept from the previous sweep (V = I cold):
+//   1. T = (3 I - V^H V) / 2          Newton-Schulz step against float32 drift of V
+//   2. V1 = V T
+//   3. W = C V1,  A = V1^H W           A is diagonal up to the change since the last sweep
+//   4. Jacobi on A (SIMT, one CTA per matrix) from Q = I, with the first-order stop: it leaves
+//      M = diag(max(l, 0)), or M = f(L) + L o E when the off-diagonal part E is small enough
+//      (Daleckii-Krein, see dk_stop in ve_device.cuh), and the rotations Q
+//   5. V2 = V1 Q (kept for the next sweep),  Y = V2 M V2^H
+// Steps 1-3 and 5 are seven batched tensor-core products; only step 4 runs on the SIMT pipes.
+// Every matrix is held "split" (hi = tf32 part, lo = remainder) in the KC4 layout of
+// ve_tcgemm.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ve_device.cuh"
+#include "ve_internal.h"
+#include "ve_tc.cuh"
+
+namespace ve {
+
+namespace {
+
+constexpr int kN = 256, kPl = kN * kN, kLD = kN + 1, kNT = 512;
+
+__device__ __forceinline__ void split4(const float* v, float4& hi, float4& lo) {
+  hi = make_float4(tc::tf32_hi(v[0]), tc::tf32_hi(v[1]), tc::tf32_hi(v[2]), tc::tf32_hi(v[3]));
+  lo = make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
+}
+
+// Identity in split form (the cold start V = I) for `count` matrices of `npl` planes.
+__global__ void k_tc_identity(float* V, float* Vt, long count, int npl) {
+  const long total = count * npl * (long)(kPl / 4);
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+    const long mat = q / (npl * (kPl / 4));
+    const int rem = (int)(q % (npl * (kPl / 4)));
+    const int pl = rem / (kPl / 4), c4 = rem % (kPl / 4);  // c4 = chunk * 256 + row
+    const int r = c4 % kN, k0 = (c4 / kN) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pl == 0) {
+      v.x = (r == k0) ? 1.f : 0.f;
+      v.y = (r == k0 + 1) ? 1.f : 0.f;
+      v.z = (r == k0 + 2) ? 1.f : 0.f;
+      v.w = (r == k0 + 3) ? 1.f : 0.f;
+    }
+    const size_t off = ((size_t)mat * npl + pl) * kPl + (size_t)c4 * 4;
+    *reinterpret_cast<float4*>(V + off) = v;
+    *reinterpret_cast<float4*>(Vt + off) = v;
+  }
+}
+
+template <bool CPLX>
+struct JShape {
+  static constexpr size_t MAT = ((sizeof(float) * kN * kLD + 255) / 256) * 256;
+  static constexpr int NMAT = CPLX ? 4 : 2;
+  static constexpr size_t bytes = NMAT * MAT + 4096;
+};
+
+// Step 4: one CTA of 512 threads per matrix, the matrix and its rotations staged in a per-CTA
+// slice of a global workspace (L2-resident).  In: A (split, KC4).  Out: M (split, KC4) and Q^T.
+template <bool CPLX>
+__global__ void __launch_bounds__(kNT, 1)
+    k_tc_jacobi(const float* __restrict__ Ain, float* __restrict__ Mout, float* __restrict__ Qt, long count,
+                unsigned char* ws, unsigned long long* stats) {
+  using S = JShape<CPLX>;
+  constexpr int NPL = CPLX ? 4 : 2;
+  unsigned char* base = ws + (size_t)blockIdx.x * S::bytes;
+  float* Ar = reinterpret_cast<float*>(base);
+  float* Vr = reinterpret_cast<float*>(base + S::MAT);
+  float* Ai = CPLX ? reinterpret_cast<float*>(base + 2 * S::MAT) : nullptr;
+  float* Vi = CPLX ? reinterpret_cast<float*>(base + 3 * S::MAT) : nullptr;
+  float* cs = reinterpret_cast<float*>(base + S::NMAT * S::MAT);
+  float* red = cs + 2 * kN;
+  const int tid = threadIdx.x;
+  for (long b = blockIdx.x; b < count; b += gridDim.x) {
+    const float* A = Ain + (size_t)b * NPL * kPl;
+    // load hi + lo (one float4 chunk of a row per thread and step: coalesced)
+    for (int q = tid; q < kPl / 4; q += kNT) {
+      const int r = q % kN, k0 = (q / kN) * 4;
+      const float4 h = *reinterpret_cast<const float4*>(A + 4 * q);
+      const float4 l = *reinterpret_cast<const float4*>(A + kPl + 4 * q);
+      float* row = Ar + r * kLD + k0;
+      row[0] = h.x + l.x;
+      row[1] = h.y + l.y;
+      row[2] = h.z + l.z;
+      row[3] = h.w + l.w;
+      if constexpr (CPLX) {
+        const float4 hi2 = *reinterpret_cast<const float4*>(A + 2 * kPl + 4 * q);
+        const float4 lo2 = *reinterpret_cast<const float4*>(A + 3 * kPl + 4 * q);
+        float* ri = Ai + r * kLD + k0;
+        ri[0] = hi2.x + lo2.x;
+        ri[1] = hi2.y + lo2.y;
+        ri[2] = hi2.z + lo2.z;
+        ri[3] = hi2.w + lo2.w;
+      }
+    }
+    __syncthreads();
+    // (A + A^H) / 2: the product V^H C V is Hermitian only to rounding
+    for (int t = tid; t < kN * (kN + 1) / 2; t += kNT) {
+      int i, j;
+      tri_index(kN, t, i, j);
+      if (i == j) {
+        if constexpr (CPLX) Ai[i * kLD + i] = 0.f;
+        continue;
+      }
+      const float r = 0.5f * (Ar[i * kLD + j] + Ar[j * kLD + i]);
+      Ar[i * kLD + j] = r;
+      Ar[j * kLD + i] = r;
+      if constexpr (CPLX) {
+        const float im = 0.5f * (Ai[i * kLD + j] - Ai[j * kLD + i]);
+        Ai[i * kLD + j] = im;
+        Ai[j * kLD + i] = -im;
+      }
+    }
+    __syncthreads();
+    bool dk = false;
+    int nsw;
+    if constexpr (CPLX)
+      nsw = jacobi_herm<float, kN, kLD, kNT, true, true, true>(Ar, Ai, Vr, Vi, cs, red, tid, &dk);
+    else
+      nsw = jacobi_sym<float, kN, kLD, kNT, true, true, true>(Ar, Vr, cs, red, tid, &dk);
+    if (stats && tid == 0) {
+      atomicAdd(stats, (unsigned long long)nsw);
+      atomicAdd(stats + 1, 1ull);
+      if (dk) atomicAdd(stats + 2, 1ull);
+    }
+    // M: f(L) + L o E after a first-order stop, else diag(max(l, 0))
+    if (dk) {
+      if constexpr (CPLX)
+        dk_matrix_herm<float, kN, kLD, kNT>(Ar, Ai, cs, tid);
+      else
+        dk_matrix_sym<float, kN, kLD, kNT>(Ar, cs, tid);
+    } else {
+      for (int e = tid; e < kPl; e += kNT) {
+        const int i = e / kN, j = e % kN;
+        const float a = Ar[i * kLD + j];
+        Ar[i * kLD + j] = (i == j) ? (a > 0.f ? a : 0.f) : 0.f;
+        if constexpr (CPLX) Ai[i * kLD + j] = 0.f;
+      }
+      __syncthreads();
+    }
+    float* M = Mout + (size_t)b * NPL * kPl;
+    float* Q = Qt + (size_t)b * NPL * kPl;
+    for (int q = tid; q < kPl / 4; q += kNT) {
+      const int r = q % kN, k0 = (q / kN) * 4;
+      float v[4];
+      float4 hi, lo;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = Ar[r * kLD + k0 + u];
+      split4(v, hi, lo);
+      *reinterpret_cast<float4*>(M + 4 * q) = hi;
+      *reinterpret_cast<float4*>(M + kPl + 4 * q) = lo;
+      // Q^T[r][k] = Q[k][r]: the rotations accumulated in V
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = Vr[(k0 + u) * kLD + r];
+      split4(v, hi, lo);
+      *reinterpret_cast<float4*>(Q + 4 * q) = hi;
+      *reinterpret_cast<float4*>(Q + kPl + 4 * q) = lo;
+      if constexpr (CPLX) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = Ai[r * kLD + k0 + u];
+        split4(v, hi, lo);
+        *reinterpret_cast<float4*>(M + 2 * kPl + 4 * q) = hi;
+        *reinterpret_cast<float4*>(M + 3 * kPl + 4 * q) = lo;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = Vi[(k0 + u) * kLD + r];
+        split4(v, hi, lo);
+        *reinterpret_cast<float4*>(Q + 2 * kPl + 4 * q) = hi;
+        *reinterpret_cast<float4*>(Q + 3 * kPl + 4 * q) = lo;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t tc_proj_ws_bytes(long cap, int cplx) {
+  const size_t mat = (size_t)(cplx ? 4 : 2) * kPl * sizeof(float);
+  const size_t jws = (cplx ? JShape<true>::bytes : JShape<false>::bytes) * (size_t)big_grid();
+  return 9 * al256(mat * (size_t)cap) + al256(jws) + 256;
+}
+
+int tc_proj_ws_init(TcProjWs& w, long cap, int cplx, void* mem, size_t bytes) {
+  if (cap <= 0 || !mem || bytes < tc_proj_ws_bytes(cap, cplx) || ((uintptr_t)mem & 255)) return -1;
+  w = TcProjWs();
+  w.cap = cap;
+  w.cplx = cplx;
+  const size_t mat = al256((size_t)(cplx ? 4 : 2) * kPl * sizeof(float) * (size_t)cap);
+  unsigned char* p = (unsigned char*)mem;
+  float** bufs[9] = {&w.V, &w.Vt, &w.C, &w.T, &w.V1, &w.V1t, &w.Wt, &w.M, &w.Qt};
+  for (auto b : bufs) {
+    *b = (float*)p;
+    p += mat;
+  }
+  w.jws = p;
+  p += al256((cplx ? JShape<true>::bytes : JShape<false>::bytes) * (size_t)big_grid());
+  w.err = (int*)p;
+  return 0;
+}
+
+cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long* stats, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (count > w.cap) return cudaErrorInvalidValue;
+  const int npl = w.cplx ? 4 : 2;
+  cudaError_t e;
+  if (!warm) {
+    const long q = count * npl * (long)(kPl / 4);
+    const int grid = (int)((q + 255) / 256 < 4096 ? (q + 255) / 256 : 4096);
+    k_tc_identity<<<grid, 256, 0, s>>>(w.V, w.Vt, count, npl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  auto gemm = [&](const float* x, int cx, const float* y, int cy, float alpha, float beta, float* on,
+                  float* ot) {
+    TcGemm g;
+    g.x = x;
+    g.y = y;
+    g.batch = count;
+    g.cplx = w.cplx;
+    g.conj_x = cx;
+    g.conj_y = cy;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.out_n = on;
+    g.out_t = ot;
+    g.err = w.err;
+    return tc_gemm256(g, s);
+  };
+  // 1. T = 1.5 I - 0.5 V^H V   (V^H V)_ij = sum_k conj(Vt_ik) Vt_jk
+  if ((e = gemm(w.Vt, 1, w.Vt, 0, -0.5f, 1.5f, w.T, nullptr)) != cudaSuccess) return e;
+  // 2. V1 = V T: the right factor enters as T^T = conj(T)
+  if ((e = gemm(w.V, 0, w.T, 1, 1.f, 0.f, w.V1, w.V1t)) != cudaSuccess) return e;
+  // 3. W = C V1 (kept as W^T), then A = V1^H W into T's storage
+  if ((e = gemm(w.C, 0, w.V1t, 0, 1.f, 0.f, nullptr, w.Wt)) != cudaSuccess) return e;
+  float* A = w.T;
+  if ((e = gemm(w.V1t, 1, w.Wt, 0, 1.f, 0.f, A, nullptr)) != cudaSuccess) return e;
+  // 4. Jacobi from Q = I with the first-order stop: M and Q^T
+  const int grid = (int)(count < big_grid() ? count : big_grid());
+  if (w.cplx)
+    k_tc_jacobi<true><<<grid, kNT, 0, s>>>(A, w.M, w.Qt, count, w.jws, stats);
+  else
+    k_tc_jacobi<false><<<grid, kNT, 0, s>>>(A, w.M, w.Qt, count, w.jws, stats);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 5. V2 = V1 Q (the stored eigenvectors), Z = V2 M into C, Y = Z V2^H into Wt
+  if ((e = gemm(w.V1, 0, w.Qt, 0, 1.f, 0.f, w.V, w.Vt)) != cudaSuccess) return e;
+  if ((e = gemm(w.V, 0, w.M, 1, 1.f, 0.f, w.C, nullptr)) != cudaSuccess) return e;
+  return gemm(w.C, 0, w.V, 1, 1.f, 0.f, w.Wt, nullptr);
+}
+
+}  // namespace ve

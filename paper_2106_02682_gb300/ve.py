@@ -21,6 +21,7 @@ VE_ENOMEM = -2
 VE_ECUDA = -3
 VE_ENONFINITE = -4
 VE_EUNSUPPORTED = -5
+VE_ETIMEOUT = -6
 VE_PREC_FP64 = 0
 VE_PREC_MIXED = 1
 VE_PREC_DF64 = 2
@@ -113,6 +114,7 @@ def _load():
         "ve_profile": (c_int, [H, c_int]),
         "ve_profile_read": (c_int, [H, P_double, ctypes.POINTER(c_long)]),
         "ve_profile_sweeps": (c_int, [H, P_double, P_double]),
+        "ve_profile_first_order": (c_int, [H, ctypes.POINTER(c_long), ctypes.POINTER(c_long)]),
         "ve_create_batch": (c_int, [c_int, ctypes.POINTER(ve_lattice), ctypes.POINTER(ve_cluster),
                                     ctypes.POINTER(ve_hamiltonian), ctypes.POINTER(ve_options),
                                     ctypes.POINTER(c_void_p)]),
@@ -302,6 +304,14 @@ def ve_profile_sweeps(h):
     _check(_lib.ve_profile_sweeps(c_void_p(h), ctypes.byref(a), ctypes.byref(b)),
            "ve_profile_sweeps")
     return a.value, b.value
+
+
+def ve_profile_first_order(h):
+    """((first-order stops, eigensolves) of the pair projections, (same) of the wavevector
+    projections) over the profiled sweeps."""
+    p, k = (c_long * 2)(), (c_long * 2)()
+    _check(_lib.ve_profile_first_order(c_void_p(h), p, k), "ve_profile_first_order")
+    return (p[0], p[1]), (k[0], k[1])
 
 
 def ve_project_psd_sym(in_ptr, out_ptr, n, count, precision=VE_PREC_FP64, stream=None):

@@ -71,7 +71,7 @@ def test_defaults_and_error_strings(ve):
     opt = ve.ve_default_options()
     assert (opt.mu, opt.nu, opt.eps, opt.precision, opt.check_every) == (10.0, 10.0, 2.0, 0, 10)
     assert opt.stream is None
-    for code in (0, 1, -1, -2, -3, -4, -5):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6):
         assert ve.ve_error_string(code) and ve.ve_error_string(code) != "unknown status"
     assert ve.ve_error_string(42) == "unknown status"
 
