@@ -834,6 +834,108 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, b
   return sweep;
 }
 
+// ---------------------------------------------------------------- 16 x 16 warp products
+// One warp computes a 16 x 16 product with lane l owning the 2 x 4 output tile at rows
+// 2 (l / 4), 2 (l / 4) + 1 and columns 4 (l % 4) .. + 3: eight independent accumulator chains
+// and six shared-memory reads per eight multiply-adds (a lane computing single outputs needs two
+// reads per multiply-add and has one chain).  TA / TB take the operand transposed (element
+// (i, k) of op(A) is A[k][i]); CA / CB conjugate it (complex forms).  The caller stores the
+// accumulators after a __syncwarp when the output aliases an operand.
+template <typename T, bool TA, bool TB>
+__device__ __forceinline__ void rgemm16(const T* A, int lda, const T* B, int ldb, T (&acc)[2][4],
+                                        int lane, const T* scale = nullptr) {
+  const int r0 = 2 * (lane >> 2), c0 = 4 * (lane & 3);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[a][u] = T(0);
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    T a0 = TA ? A[k * lda + r0] : A[r0 * lda + k];
+    T a1 = TA ? A[k * lda + r0 + 1] : A[(r0 + 1) * lda + k];
+    if (scale) {  // op(A) diag(scale)
+      a0 = a0 * scale[k];
+      a1 = a1 * scale[k];
+    }
+    T b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = TB ? B[(c0 + u) * ldb + k] : B[k * ldb + c0 + u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[0][u] += a0 * b[u];
+      acc[1][u] += a1 * b[u];
+    }
+  }
+}
+
+template <typename T, bool TA, bool CA, bool TB, bool CB>
+__device__ __forceinline__ void cgemm16(const T* Ar, const T* Ai, int lda, const T* Br, const T* Bi,
+                                        int ldb, T (&cr)[2][4], T (&ci)[2][4], int lane,
+                                        const T* scale = nullptr) {
+  const int r0 = 2 * (lane >> 2), c0 = 4 * (lane & 3);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cr[a][u] = T(0);
+      ci[a][u] = T(0);
+    }
+#pragma unroll 2
+  for (int k = 0; k < 16; ++k) {
+    T xr[2], xi[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int o = TA ? k * lda + r0 + a : (r0 + a) * lda + k;
+      xr[a] = Ar[o];
+      xi[a] = CA ? -Ai[o] : Ai[o];
+      if (scale) {  // op(A) diag(scale), scale real
+        xr[a] = xr[a] * scale[k];
+        xi[a] = xi[a] * scale[k];
+      }
+    }
+    T yr[4], yi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int o = TB ? (c0 + u) * ldb + k : k * ldb + c0 + u;
+      yr[u] = Br[o];
+      yi[u] = CB ? -Bi[o] : Bi[o];
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cr[a][u] += xr[a] * yr[u] - xi[a] * yi[u];
+        ci[a][u] += xr[a] * yi[u] + xi[a] * yr[u];
+      }
+  }
+}
+
+// Make a 16 x 16 matrix exactly symmetric (Hermitian when Ai is given) from its upper triangle.
+template <typename T>
+__device__ __forceinline__ void mirror16(T* Ar, T* Ai, int ld, int lane) {
+  __syncwarp();
+  for (int e = lane; e < 256; e += 32) {
+    const int i = e >> 4, j = e & 15;
+    if (i > j) {
+      Ar[i * ld + j] = Ar[j * ld + i];
+      if (Ai) Ai[i * ld + j] = -Ai[j * ld + i];
+    } else if (i == j && Ai) {
+      Ai[i * ld + i] = T(0);
+    }
+  }
+  __syncwarp();
+}
+
+// Store a 2 x 4 lane tile of a 16 x 16 result (row-major, leading dimension ld).
+template <typename T>
+__device__ __forceinline__ void store16(T* C, int ld, const T (&acc)[2][4], int lane) {
+  const int r0 = 2 * (lane >> 2), c0 = 4 * (lane & 3);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) C[(r0 + a) * ld + c0 + u] = acc[a][u];
+}
+
 // Threads per group, leading dimension and staging of an n x n matrix.  n <= 16: one warp;
 // n = 64: one CTA of 256 threads; n = 256: one CTA of 512 threads whose matrices are staged in a
 // per-CTA slice of a global workspace (1 MB per float64 matrix and its eigenvectors does not fit

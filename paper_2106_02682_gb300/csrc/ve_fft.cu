@@ -233,6 +233,9 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
             unsigned long long* stats, unsigned char* gws, const long long* iter) {
   constexpr int NT = GroupShape<D>::NT, LD = GroupShape<D>::LD;
   constexpr int GPC = GroupShape<D>::GPC;
+  // register-tiled warp products (cgemm16) in float32 only: they compute whole 16 x 16 results
+  // where the loops below compute triangles, and float64 / double-float issue is the bound there
+  constexpr bool TILE16 = D == 16 && NT == 32 && std::is_same<T, float>::value;
   using S = XSmem<D, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
@@ -261,7 +264,27 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
         Vi[(e / D) * LD + (e % D)] = vi[e];
       }
       gsync<NT>();
-      if (ns_due<T>(iter)) {
+      if (ns_due<T>(iter) && TILE16) {
+        // as below, register-tiled warp products
+        T gr[2][4], gi[2][4];
+        cgemm16<T, true, true, false, false>(Vr, Vi, LD, Vr, Vi, LD, gr, gi, tid);
+        const int r0 = 2 * (tid >> 2), c0 = 4 * (tid & 3);
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            gr[x][u] = ((r0 + x == c0 + u) ? T(1.5) : T(0)) - T(0.5) * gr[x][u];
+            gi[x][u] = -T(0.5) * gi[x][u];
+          }
+        store16(Wr, LD, gr, tid);
+        store16(Wi, LD, gi, tid);
+        __syncwarp();
+        cgemm16<T, false, false, false, false>(Vr, Vi, LD, Wr, Wi, LD, gr, gi, tid);
+        __syncwarp();
+        store16(Vr, LD, gr, tid);
+        store16(Vi, LD, gi, tid);
+        __syncwarp();
+      } else if (ns_due<T>(iter)) {
         // one Newton-Schulz step V <- V (3 I - V^H V) / 2 against the rounding drift of the
         // stored eigenvectors (Wr/Wi hold the Gram correction, Ar/Ai the new V)
         for (int e = tid; e < D * D; e += NT) {
@@ -298,7 +321,19 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
       }
     }
     unpack_block<D, NT, LD, T>(spec, s, s2, E, Ar, Ai, tid);
-    if (warm && vr) {
+    if (warm && vr && TILE16) {
+      // A <- V^H C V with register-tiled warp products (upper triangle mirrored)
+      T xr[2][4], xi[2][4];
+      cgemm16<T, false, false, false, false>(Ar, Ai, LD, Vr, Vi, LD, xr, xi, tid);
+      store16(Wr, LD, xr, tid);
+      store16(Wi, LD, xi, tid);
+      __syncwarp();
+      cgemm16<T, true, true, false, false>(Vr, Vi, LD, Wr, Wi, LD, xr, xi, tid);
+      store16(Ar, LD, xr, tid);
+      store16(Ai, LD, xi, tid);
+      mirror16<T>(Ar, Ai, LD, tid);
+      nsw = jacobi_herm<T, D, LD, NT, true, false, true>(Ar, Ai, Vr, Vi, cs, red, tid, &dk);
+    } else if (warm && vr) {
       // start from the previous eigenvectors: A <- V^H C V
       for (int e = tid; e < D * D; e += NT) {  // W = C V
         const int i = e / D, jj = e % D;
@@ -344,7 +379,30 @@ __global__ void __launch_bounds__(GroupShape<D>::NT * GroupShape<D>::GPC, GroupS
         vi[e] = Vi[(e / D) * LD + (e % D)];
       }
     }
-    if (dk) {
+    if (TILE16) {
+      // Y = V M V^H (M = f(Lambda) + L o E after a first-order stop, else diag(max(l, 0)))
+      // with register-tiled warp products; the upper triangle is mirrored
+      T yr[2][4], yi[2][4];
+      if (dk) {
+        dk_matrix_herm<T, D, LD, NT>(Ar, Ai, cs, tid);
+        cgemm16<T, false, false, false, false>(Vr, Vi, LD, Ar, Ai, LD, yr, yi, tid);
+        store16(Wr, LD, yr, tid);
+        store16(Wi, LD, yi, tid);
+        __syncwarp();
+        cgemm16<T, false, false, true, true>(Wr, Wi, LD, Vr, Vi, LD, yr, yi, tid);
+      } else {
+        for (int k = tid; k < D; k += NT) {
+          const T w = Ar[k * LD + k];
+          W[k] = w > T(0) ? w : T(0);
+        }
+        __syncwarp();
+        cgemm16<T, false, false, true, true>(Vr, Vi, LD, Vr, Vi, LD, yr, yi, tid, W);
+      }
+      __syncwarp();
+      store16(Ar, LD, yr, tid);
+      store16(Ai, LD, yi, tid);
+      mirror16<T>(Ar, Ai, LD, tid);
+    } else if (dk) {
       // Y = V M V^H with M = f(Lambda) + L o E (dk_stop): W = V M, then W V^H
       dk_matrix_herm<T, D, LD, NT>(Ar, Ai, cs, tid);
       for (int e = tid; e < D * D; e += NT) {

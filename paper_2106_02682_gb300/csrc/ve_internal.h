@@ -30,9 +30,10 @@ inline cudaError_t smem_once(K kernel, size_t bytes, unsigned long long& mask) {
 // erodes their orthogonality a little every sweep; a drifted V makes V^T C V a non-similarity
 // and the projection inexact by as much.  A Newton-Schulz step V <- V (3 I - V^T V) / 2 squares
 // the drift: every sweep in float32, every NS_EVERY-th sweep in float64 and double-float words
-// (measured: the float64 state after 300 sweeps then agrees with the oracle to ~3e-13 instead of
-// ~1e-10 at D = 64, 256).
-constexpr int NS_EVERY = 8;
+// (measured with a step every sweep: the float64 state after 300 sweeps agrees with the oracle to
+// ~3e-13 instead of ~1e-10 at D = 64, 256; the drift between steps grows linearly, so a step every
+// 16 sweeps keeps it far below the 1e-10 target at 1/16 of the cost).
+constexpr int NS_EVERY = 16;
 template <typename T>
 __device__ __forceinline__ bool ns_due(const long long* iter) {
   if (sizeof(T) == 4) return true;
@@ -189,8 +190,17 @@ struct TcGemm {
   float* out_n = nullptr;
   float* out_t = nullptr;
   int* err = nullptr;
+  int round = 0;     // tc_rot256: the block-Jacobi round
+  int conj_out = 0;  // conjugate the result before writing it
 };
 cudaError_t tc_gemm256(const TcGemm& g, cudaStream_t s);
+// Block Jacobi on 256 x 256 matrices: TC_BJ_NB blocks of TC_BJ_BS indices, paired by the circle
+// ordering (rr_pair(TC_BJ_NB, round, k)), TC_BJ_NB - 1 rounds a sweep.
+constexpr int TC_BJ_BS = 16, TC_BJ_NB = 256 / TC_BJ_BS;
+// x_b R_b for a block rotation R of round g.round, R nonzero only on each pair's 2 TC_BJ_BS square
+// block.  g.y holds R^T; only its pairs' row slices are read, and each output column block
+// accumulates over its pair's indices: 2 TC_BJ_BS / 256 of the products of tc_gemm256.
+cudaError_t tc_rot256(const TcGemm& g, cudaStream_t s);
 
 // Batched float32 PSD projection of 256 x 256 matrices with the products on the tensor cores
 // (ve_tcproj.cu).  One workspace serves up to `cap` matrices of one kind (real or complex); V and

@@ -49,12 +49,14 @@ __global__ void k_gemm(int M, int N, int K, const float* __restrict__ A, int lda
   }
 }
 
-// d = (y - t) * scale; also accumulates sum (y - t)^2 into loss[0] (one atomic per block)
+// d = (y - t) * scale.  One CTA of 256 threads also forms sum (y - t)^2 into loss[0] in a fixed
+// order (thread-strided partial sums, then a tree), so the reported loss is reproducible bit for
+// bit; the gradient itself never depended on an order of atomics.
 __global__ void k_out_grad(int n, const float* y, const float* t, float* d, float scale,
                            float* loss) {
   __shared__ float red[256];
   float s = 0.f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const float r = y[i] - t[i];
     d[i] = r * scale;
     s += r * r;
@@ -65,7 +67,7 @@ __global__ void k_out_grad(int n, const float* y, const float* t, float* d, floa
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+  if (threadIdx.x == 0) loss[0] = red[0];
 }
 
 // dz = da * (1 - a^2)  (tanh derivative, in place on da)
@@ -170,8 +172,7 @@ cudaError_t backward(ve_mlp* m, int n) {
   if (e != cudaSuccess) return e;
   const int no = n * m->n_out;
   const float scale = 1.f / (float)no;
-  k_out_grad<<<(no + 255) / 256 < 256 ? (no + 255) / 256 : 256, 256, 0, m->s>>>(no, m->act[L], m->t,
-                                                                               m->d0, scale, m->loss);
+  k_out_grad<<<1, 256, 0, m->s>>>(no, m->act[L], m->t, m->d0, scale, m->loss);
   float* dz = m->d0;
   float* other = m->d1;
   for (int l = L - 1; l >= 0; --l) {

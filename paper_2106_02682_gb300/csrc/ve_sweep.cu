@@ -57,6 +57,9 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
     k_pair(const PairArgs a) {
   constexpr int m = PairShape<D>::m, NT = PairShape<D>::NT, LD = PairShape<D>::LD;
   constexpr int GPC = PairShape<D>::GPC;
+  // register-tiled warp products (rgemm16) in float32 only: they compute whole 16 x 16 results
+  // where the loops below compute triangles, and float64 / double-float issue is the bound there
+  constexpr bool TILE16 = D == 16 && NT == 32 && std::is_same<T, float>::value;
   using S = PairSmem<D, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / NT, tid = threadIdx.x % NT;
@@ -143,7 +146,22 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
     if (a.warm) {
       for (int e = tid; e < D * D; e += NT) V[(e / D) * LD + (e % D)] = vs[e];
       gsync<NT>();
-      if (ns_due<T>(a.iter)) {
+      if (ns_due<T>(a.iter) && TILE16) {
+        // as below, register-tiled warp products
+        T acc[2][4];
+        rgemm16<T, true, false>(V, LD, V, LD, acc, tid);
+        const int r0 = 2 * (tid >> 2), c0 = 4 * (tid & 3);
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[x][u] = ((r0 + x == c0 + u) ? T(1.5) : T(0)) - T(0.5) * acc[x][u];
+        store16(Wt, LD, acc, tid);
+        __syncwarp();
+        rgemm16<T, false, false>(V, LD, Wt, LD, acc, tid);
+        __syncwarp();
+        store16(V, LD, acc, tid);
+        __syncwarp();
+      } else if (ns_due<T>(a.iter)) {
         // rotations erode V's orthogonality over many sweeps; one Newton-Schulz step
         // V <- V (3 I - V^T V) / 2 squares the error before V is used (A and Wt as scratch)
         for (int e = tid; e < D * D; e += NT) {
@@ -174,7 +192,17 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
       A[j * LD + i] = v;
     }
     gsync<NT>();
-    if (a.warm) {
+    if (a.warm && TILE16) {
+      // A <- V^T C V with register-tiled warp products (upper triangle mirrored)
+      T acc[2][4];
+      rgemm16<T, false, false>(A, LD, V, LD, acc, tid);
+      store16(Wt, LD, acc, tid);
+      __syncwarp();
+      rgemm16<T, true, false>(V, LD, Wt, LD, acc, tid);
+      store16(A, LD, acc, tid);
+      mirror16<T>(A, nullptr, LD, tid);
+      nsw = jacobi_sym<T, D, LD, NT, true, false, true>(A, V, cs, red, tid, &dk);
+    } else if (a.warm) {
       // start from the previous eigenvectors: A <- V^T C V
       for (int e = tid; e < D * D; e += NT) {
         const int i = e / D, j = e % D;
@@ -204,7 +232,28 @@ __global__ void __launch_bounds__(PairShape<D>::NT * PairShape<D>::GPC, GroupSha
       if (dk) atomicAdd(a.stats + 2, 1ull);
     }
     for (int e = tid; e < D * D; e += NT) vs[e] = V[(e / D) * LD + (e % D)];
-    if (dk) {
+    if (TILE16) {
+      // rho~ = V M V^T (M = f(Lambda) + L o E after a first-order stop, else diag(max(l, 0)))
+      // with register-tiled warp products; the upper triangle is mirrored
+      T acc[2][4];
+      if (dk) {
+        dk_matrix_sym<T, D, LD, NT>(A, cs, tid);
+        rgemm16<T, false, false>(V, LD, A, LD, acc, tid);
+        store16(Wt, LD, acc, tid);
+        __syncwarp();
+        rgemm16<T, false, true>(Wt, LD, V, LD, acc, tid);
+      } else {
+        for (int k = tid; k < D; k += NT) {
+          const T w = A[k * LD + k];
+          W[k] = w > T(0) ? w : T(0);
+        }
+        __syncwarp();
+        rgemm16<T, false, true>(V, LD, V, LD, acc, tid, W);
+      }
+      __syncwarp();
+      store16(A, LD, acc, tid);
+      mirror16<T>(A, nullptr, LD, tid);
+    } else if (dk) {
       // rho~ = V M V^T with M = f(Lambda) + L o E (dk_stop): Wt = V M, then Wt V^T
       dk_matrix_sym<T, D, LD, NT>(A, cs, tid);
       for (int e = tid; e < D * D; e += NT) {

@@ -34,16 +34,21 @@ namespace {
 
 using namespace tc;
 
-template <bool CPLX>
+// ROT: the right factor is a block rotation R (see tc_rot256): only the TC_BJ_BS-row slices of
+// y = R^T that hold a pair's blocks are loaded, two per stage; a stage's K slice is one block.
+template <bool CPLX, bool ROT = false>
 struct TcCfg {
   static constexpr int NPL = CPLX ? 4 : 2;            // planes of a split matrix
   static constexpr int KS = 16;                       // K elements per stage
-  static constexpr int STAGES = CPLX ? 2 : 4;
   static constexpr int XB = 128 * KS * 4;             // bytes of one X plane slice (128 rows)
-  static constexpr int YB = 256 * KS * 4;             // bytes of one Y plane slice (256 rows)
-  static constexpr int STAGE_BYTES = NPL * (XB + YB);
+  static constexpr int YR = ROT ? TC_BJ_BS : 256;     // rows of one Y plane slice
+  static constexpr int YB = YR * KS * 4;              // bytes of one Y plane slice
+  static constexpr int NYS = ROT ? 2 : 1;             // Y slices per plane and stage
+  static constexpr int STAGE_BYTES = NPL * (XB + NYS * YB);
+  static constexpr int STAGES = (CPLX && !ROT) ? 2 : 4;
   static constexpr int TMEM_COLS = CPLX ? 512 : 256;  // re and im accumulators, 256 columns each
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2048;  // + alignment, barriers
+  static constexpr int XSTAGE = 4 * 32 * 17 * 4;   // epilogue transpose staging, 32 x 16 per warp
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + XSTAGE;  // + align, barriers
 };
 
 constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
@@ -52,6 +57,8 @@ constexpr int kPlane = 256 * 256;
 struct TcParams {
   long batch;
   int conj_x, conj_y;
+  int round;     // ROT: the block-Jacobi round whose pairs R rotates
+  int conj_out;  // conjugate the result before it is written
   float alpha, beta;
   float* out_n;
   float* out_t;
@@ -61,10 +68,25 @@ struct TcParams {
 // Element (r, k) of a KC4 plane.
 __device__ __forceinline__ int kc4(int r, int k) { return ((k >> 2) * 256 + r) * 4 + (k & 3); }
 
-template <bool CPLX>
+// Pair k of round r of the circle ordering of the TC_BJ_NB column blocks (p < q), as rr_pair.
+__device__ __forceinline__ void block_pair(int r, int k, int& p, int& q) {
+  constexpr int n = TC_BJ_NB;
+  int a, b;
+  if (k == 0) {
+    a = n - 1;
+    b = r;
+  } else {
+    a = (r + k) % (n - 1);
+    b = (r - k + n - 1) % (n - 1);
+  }
+  p = a < b ? a : b;
+  q = a < b ? b : a;
+}
+
+template <bool CPLX, bool ROT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tcgemm(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap my, const TcParams p) {
-  using C = TcCfg<CPLX>;
+  using C = TcCfg<CPLX, ROT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + C::STAGES * C::STAGE_BYTES);
@@ -74,6 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drain = tempty + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  float* xst = reinterpret_cast<float*>(base + C::STAGES * C::STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long ntiles = 2 * p.batch;
@@ -114,10 +137,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           iph = (iph & ~(1u << s)) | (ph << s);
           mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
           unsigned char* st = base + s * C::STAGE_BYTES;
+          // K slice of this stage; ROT: stage kb is block (kb & 1 ? q : p) of pair kb / 2
+          static_assert(!ROT || TC_BJ_BS == C::KS, "a rotation stage spans one block");
+          int kslice = kb, bp = 0, bq = 0;
+          if constexpr (ROT) {
+            block_pair(p.round, kb >> 1, bp, bq);
+            kslice = (kb & 1) ? bq : bp;
+          }
           for (int pl = 0; pl < C::NPL; ++pl) {
-            tma_load_4d(st + pl * C::XB, &mx, &full[s], 0, 128 * h, kb * (C::KS / 4), b * C::NPL + pl);
-            tma_load_4d(st + C::NPL * C::XB + pl * C::YB, &my, &full[s], 0, 0, kb * (C::KS / 4),
-                        b * C::NPL + pl);
+            tma_load_4d(st + pl * C::XB, &mx, &full[s], 0, 128 * h, kslice * (C::KS / 4), b * C::NPL + pl);
+            if constexpr (ROT) {
+              // the rows of R^T (columns of R) in the pair's two blocks
+              tma_load_4d(st + C::NPL * C::XB + (0 * C::NPL + pl) * C::YB, &my, &full[s], 0,
+                          TC_BJ_BS * bp, kslice * (C::KS / 4), b * C::NPL + pl);
+              tma_load_4d(st + C::NPL * C::XB + (1 * C::NPL + pl) * C::YB, &my, &full[s], 0,
+                          TC_BJ_BS * bq, kslice * (C::KS / 4), b * C::NPL + pl);
+            } else {
+              tma_load_4d(st + C::NPL * C::XB + pl * C::YB, &my, &full[s], 0, 0, kslice * (C::KS / 4),
+                          b * C::NPL + pl);
+            }
           }
           if (++s == C::STAGES) {
             s = 0;
@@ -136,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer
-      constexpr uint32_t XLBO = 128 * 16, YLBO = 256 * 16, SBO = 128;
+      constexpr uint32_t XLBO = 128 * 16, YLBO = C::YR * 16, SBO = 128;
       // products of one K step: (x plane, y plane, accumulator column, negate)
       // real: hi hi, hi lo, lo hi.  Complex x = xr + i sx xi, y = yr + i sy yi (s = -1 when
       // conjugated): Dr = xr yr^T - sx sy xi yi^T, Di = sy xr yi^T + sx xi yr^T.
@@ -155,34 +193,44 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t st = smem_u32(base + s * C::STAGE_BYTES);
-          const uint32_t xs = st, ys = st + C::NPL * C::XB;
+          const uint32_t xs = st, ys0 = st + C::NPL * C::XB;
+          // ROT: the stage's K slice feeds the output columns of both blocks of its pair, each
+          // accumulated only over the pair's 2 stages (R is zero elsewhere): N = TC_BJ_BS
+          int bp = 0, bq = 0;
+          if constexpr (ROT) block_pair(p.round, kb >> 1, bp, bq);
 #pragma unroll
-          for (int ks = 0; ks < C::KS / 8; ++ks) {
-            auto mma = [&](int xp, int yp, uint32_t col, int neg, bool first) {
-              const uint64_t ad = smem_desc(xs + xp * C::XB + ks * 2 * XLBO, XLBO, SBO);
-              const uint64_t bd = smem_desc(ys + yp * C::YB + ks * 2 * YLBO, YLBO, SBO);
-              mma_tf32(tmem + col, ad, bd, idesc_tf32(128, 256, neg, 0), first ? 0u : 1u);
-            };
-            const bool f0 = kb == 0 && ks == 0;
-            if constexpr (!CPLX) {
-              mma(0, 0, 0, 0, f0);
-              mma(0, 1, 0, 0, false);
-              mma(1, 0, 0, 0, false);
-            } else {
-              const int nr = (sx * sy > 0) ? 1 : 0;  // Dr: - sx sy xi yi^T
-              mma(0, 0, 0, 0, f0);
-              mma(0, 1, 0, 0, false);
-              mma(1, 0, 0, 0, false);
-              mma(2, 2, 0, nr, false);
-              mma(2, 3, 0, nr, false);
-              mma(3, 2, 0, nr, false);
-              const int ni1 = sy < 0 ? 1 : 0, ni2 = sx < 0 ? 1 : 0;
-              mma(0, 2, 256, ni1, f0);
-              mma(0, 3, 256, ni1, false);
-              mma(1, 2, 256, ni1, false);
-              mma(2, 0, 256, ni2, false);
-              mma(2, 1, 256, ni2, false);
-              mma(3, 0, 256, ni2, false);
+          for (int cb = 0; cb < C::NYS; ++cb) {
+            const uint32_t ys = ys0 + cb * C::NPL * C::YB;
+            const uint32_t c0 = ROT ? (uint32_t)TC_BJ_BS * (uint32_t)(cb ? bq : bp) : 0u;
+            constexpr int NN = ROT ? TC_BJ_BS : 256;
+#pragma unroll
+            for (int ks = 0; ks < C::KS / 8; ++ks) {
+              auto mma = [&](int xp, int yp, uint32_t col, int neg, bool first) {
+                const uint64_t ad = smem_desc(xs + xp * C::XB + ks * 2 * XLBO, XLBO, SBO);
+                const uint64_t bd = smem_desc(ys + yp * C::YB + ks * 2 * YLBO, YLBO, SBO);
+                mma_tf32(tmem + c0 + col, ad, bd, idesc_tf32(128, NN, neg, 0), first ? 0u : 1u);
+              };
+              const bool f0 = (ROT ? (kb & 1) == 0 : kb == 0) && ks == 0;
+              if constexpr (!CPLX) {
+                mma(0, 0, 0, 0, f0);
+                mma(0, 1, 0, 0, false);
+                mma(1, 0, 0, 0, false);
+              } else {
+                const int nr = (sx * sy > 0) ? 1 : 0;  // Dr: - sx sy xi yi^T
+                mma(0, 0, 0, 0, f0);
+                mma(0, 1, 0, 0, false);
+                mma(1, 0, 0, 0, false);
+                mma(2, 2, 0, nr, false);
+                mma(2, 3, 0, nr, false);
+                mma(3, 2, 0, nr, false);
+                const int ni1 = sy < 0 ? 1 : 0, ni2 = sx < 0 ? 1 : 0;
+                mma(0, 2, 256, ni1, f0);
+                mma(0, 3, 256, ni1, false);
+                mma(1, 2, 256, ni1, false);
+                mma(2, 0, 256, ni2, false);
+                mma(2, 1, 256, ni2, false);
+                mma(3, 0, 256, ni2, false);
+              }
             }
           }
           mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
@@ -219,10 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         float vr[16], vi[16];
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + n0, vr);
         if constexpr (CPLX) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 256 + n0, vi);
+        const float ci = p.conj_out ? -p.alpha : p.alpha;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           vr[j] = p.alpha * vr[j] + ((gr == n0 + j) ? p.beta : 0.f);
-          if constexpr (CPLX) vi[j] = p.alpha * vi[j];
+          if constexpr (CPLX) vi[j] = ci * vi[j];
         }
         if (on) {
 #pragma unroll
@@ -254,17 +303,29 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (ot) {
+          // D^T through a per-warp shared-memory tile: the warp holds rows gr0 .. gr0 + 31 and
+          // columns n0 .. n0 + 15; in D^T's KC4 layout a 4-row chunk of one column is one float4,
+          // and the 16 columns of a chunk are 256 contiguous bytes, so each half-warp stores one
+          // chunk row in one contiguous segment.
+          float* tile = xst + q * (32 * 17);
+          const int gr0 = 128 * h + 32 * q;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int off = kc4(n0 + j, gr);
-            const float hr = tf32_hi(vr[j]);
-            ot[off] = hr;
-            ot[kPlane + off] = vr[j] - hr;
-            if constexpr (CPLX) {
-              const float hi2 = tf32_hi(vi[j]);
-              ot[2 * kPlane + off] = hi2;
-              ot[3 * kPlane + off] = vi[j] - hi2;
+          for (int part = 0; part < (CPLX ? 4 : 2); ++part) {
+            const float* v = (part < 2) ? vr : vi;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float hv = tf32_hi(v[j]);
+              tile[lane * 17 + j] = (part & 1) ? v[j] - hv : hv;
             }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int qq = lane + 32 * i, c = qq >> 4, n = qq & 15;
+              const float4 w4 = make_float4(tile[(4 * c) * 17 + n], tile[(4 * c + 1) * 17 + n],
+                                            tile[(4 * c + 2) * 17 + n], tile[(4 * c + 3) * 17 + n]);
+              *reinterpret_cast<float4*>(ot + part * kPlane + ((gr0 / 4 + c) * 256 + n0 + n) * 4) = w4;
+            }
+            __syncwarp();
           }
         }
       }
@@ -320,23 +381,25 @@ int sm_count() {
   return n;
 }
 
-template <bool CPLX>
+template <bool CPLX, bool ROT>
 cudaError_t launch(const TcGemm& g, cudaStream_t s) {
-  using C = TcCfg<CPLX>;
+  using C = TcCfg<CPLX, ROT>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tcgemm<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tcgemm<CPLX, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   CUtensorMap mx, my;
-  if (!make_map(&mx, g.x, g.batch * C::NPL, 128) || !make_map(&my, g.y, g.batch * C::NPL, 256))
+  if (!make_map(&mx, g.x, g.batch * C::NPL, 128) || !make_map(&my, g.y, g.batch * C::NPL, C::YR))
     return cudaErrorInvalidValue;
   TcParams p;
   p.batch = g.batch;
   p.conj_x = g.conj_x;
   p.conj_y = g.conj_y;
+  p.round = g.round;
+  p.conj_out = g.conj_out;
   p.alpha = g.alpha;
   p.beta = g.beta;
   p.out_n = g.out_n;
@@ -344,7 +407,7 @@ cudaError_t launch(const TcGemm& g, cudaStream_t s) {
   p.err = g.err;
   const long tiles = 2 * g.batch;
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-  k_tcgemm<CPLX><<<grid, kThreads, C::SMEM, s>>>(mx, my, p);
+  k_tcgemm<CPLX, ROT><<<grid, kThreads, C::SMEM, s>>>(mx, my, p);
   return cudaGetLastError();
 }
 
@@ -355,7 +418,16 @@ cudaError_t tc_gemm256(const TcGemm& g, cudaStream_t s) {
   if (!g.x || !g.y || (!g.out_n && !g.out_t)) return cudaErrorInvalidValue;
   if (((uintptr_t)g.x | (uintptr_t)g.y | (uintptr_t)g.out_n | (uintptr_t)g.out_t) & 15)
     return cudaErrorInvalidValue;
-  return g.cplx ? launch<true>(g, s) : launch<false>(g, s);
+  return g.cplx ? launch<true, false>(g, s) : launch<false, false>(g, s);
+}
+
+cudaError_t tc_rot256(const TcGemm& g, cudaStream_t s) {
+  if (g.batch <= 0) return cudaSuccess;
+  if (!g.x || !g.y || (!g.out_n && !g.out_t) || g.round < 0 || g.round > TC_BJ_NB - 2)
+    return cudaErrorInvalidValue;
+  if (((uintptr_t)g.x | (uintptr_t)g.y | (uintptr_t)g.out_n | (uintptr_t)g.out_t) & 15)
+    return cudaErrorInvalidValue;
+  return g.cplx ? launch<true, true>(g, s) : launch<false, true>(g, s);
 }
 
 }  // namespace ve

@@ -8,7 +8,8 @@
 //   1. T = (3 I - V^H V) / 2          Newton-Schulz step against float32 drift of V
 //   2. V1 = V T
 //   3. W = C V1,  A = V1^H W           A is diagonal up to the change since the last sweep
-//   4. Jacobi on A (SIMT, one CTA per matrix) from Q = I, with the first-order stop: it leaves
+//   4. block-Jacobi sweeps on A whose rotations are applied by tensor-core products (below),
+//      then scalar Jacobi (SIMT, one CTA per matrix) from Q = I with the first-order stop: it leaves
 //      M = diag(max(l, 0)), or M = f(L) + L o E when the off-diagonal part E is small enough
 //      (Daleckii-Krein, see dk_stop in ve_device.cuh), and the rotations Q
 //   5. V2 = V1 Q (kept for the next sweep),  Y = V2 M V2^H
@@ -178,6 +179,100 @@ __global__ void __launch_bounds__(kNT, 1)
   }
 }
 
+// ---- block Jacobi: the 256 indices form TC_BJ_NB = 16 blocks of TC_BJ_BS = 16; a round pairs
+// the blocks by the circle ordering (15 rounds a sweep, 8 disjoint pairs a round).  For each pair
+// (I, J) the 32 x 32 principal block A[I u J, I u J] is diagonalised exactly by one warp in shared
+// memory (k_bj_sub), its eigenvectors U placed in the round's rotation R (R[I u J, I u J] = U,
+// zero elsewhere), and A <- R^H A R, V <- V R are three tensor-core products that touch only
+// R's nonzero blocks (tc_rot256), so only those blocks of R^T are ever written.  A sweep of rounds annihilates every off-diagonal
+// block once; like scalar Jacobi it converges quadratically.
+constexpr int kBS = TC_BJ_BS, kNB = TC_BJ_NB, kSub = 2 * kBS, kSLD = kSub + 1, kSubWarps = 4;
+constexpr int kBjSweeps = 2;
+
+template <bool CPLX>
+struct SubShape {
+  static constexpr int NMAT = CPLX ? 4 : 2;
+  static constexpr size_t per_warp = sizeof(float) * (NMAT * kSub * kSLD + 2 * kSub + 32);
+  static constexpr size_t bytes = per_warp * kSubWarps;
+};
+
+__device__ __forceinline__ int kc4i(int r, int k) { return ((k >> 2) * kN + r) * 4 + (k & 3); }
+
+template <bool CPLX>
+__global__ void __launch_bounds__(32 * kSubWarps)
+    k_bj_sub(const float* __restrict__ A, float* __restrict__ Rt, long count, int round) {
+  constexpr int NPL = CPLX ? 4 : 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* Sr = reinterpret_cast<float*>(smem_raw + w * SubShape<CPLX>::per_warp);
+  float* Ur = Sr + kSub * kSLD;
+  float* Si = CPLX ? Ur + kSub * kSLD : nullptr;
+  float* Ui = CPLX ? Si + kSub * kSLD : nullptr;
+  float* cs = Sr + SubShape<CPLX>::NMAT * kSub * kSLD;
+  float* red = cs + 2 * kSub;
+  const long items = count * (kNB / 2);
+  for (long item = (long)blockIdx.x * kSubWarps + w; item < items; item += (long)gridDim.x * kSubWarps) {
+    const long b = item / (kNB / 2);
+    const int k = (int)(item % (kNB / 2));
+    int bp, bq;
+    rr_pair(kNB, round, k, bp, bq);
+    auto g = [&](int t) { return t < kBS ? bp * kBS + t : bq * kBS + (t - kBS); };
+    const float* a = A + (size_t)b * NPL * kPl;
+    for (int e = lane; e < kSub * kSub; e += 32) {
+      const int i = e / kSub, j = e % kSub;
+      const int o = kc4i(g(i), g(j));
+      Sr[i * kSLD + j] = a[o] + a[kPl + o];
+      if constexpr (CPLX) Si[i * kSLD + j] = a[2 * kPl + o] + a[3 * kPl + o];
+    }
+    __syncwarp();
+    // (S + S^H) / 2
+    for (int e = lane; e < kSub * kSub; e += 32) {
+      const int i = e / kSub, j = e % kSub;
+      if (i < j) {
+        const float v = 0.5f * (Sr[i * kSLD + j] + Sr[j * kSLD + i]);
+        Sr[i * kSLD + j] = v;
+        Sr[j * kSLD + i] = v;
+        if constexpr (CPLX) {
+          const float x = 0.5f * (Si[i * kSLD + j] - Si[j * kSLD + i]);
+          Si[i * kSLD + j] = x;
+          Si[j * kSLD + i] = -x;
+        }
+      } else if (i == j) {
+        if constexpr (CPLX) Si[i * kSLD + i] = 0.f;
+      }
+    }
+    __syncwarp();
+    if constexpr (CPLX)
+      jacobi_herm<float, kSub, kSLD, 32, true>(Sr, Si, Ur, Ui, cs, red, lane);
+    else
+      jacobi_sym<float, kSub, kSLD, 32, true>(Sr, Ur, cs, red, lane);
+    // R^T on the pair's index set: R^T[g(j)][g(t)] = U[t][j].  tc_rot256 reads R^T only there
+    // (the rows of the pair's column blocks at the pair's K slices), so the zeros elsewhere are
+    // never written.  A lane writes one 4-index chunk of one row as a float4.
+    float* rt = Rt + (size_t)b * NPL * kPl;
+    for (int e = lane; e < kSub * (kSub / 4); e += 32) {
+      const int j = e / (kSub / 4), tc = e % (kSub / 4);  // row g(j) of R^T, chunk g(4 tc)..+3
+      float ur[4], ui[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ur[u] = Ur[(4 * tc + u) * kSLD + j];
+        if constexpr (CPLX) ui[u] = Ui[(4 * tc + u) * kSLD + j];
+      }
+      const int o = ((g(4 * tc) >> 2) * kN + g(j)) * 4;
+      float4 hi, lo;
+      split4(ur, hi, lo);
+      *reinterpret_cast<float4*>(rt + o) = hi;
+      *reinterpret_cast<float4*>(rt + kPl + o) = lo;
+      if constexpr (CPLX) {
+        split4(ui, hi, lo);
+        *reinterpret_cast<float4*>(rt + 2 * kPl + o) = hi;
+        *reinterpret_cast<float4*>(rt + 3 * kPl + o) = lo;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
@@ -241,6 +336,49 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
   if ((e = gemm(w.C, 0, w.V1t, 0, 1.f, 0.f, nullptr, w.Wt)) != cudaSuccess) return e;
   float* A = w.T;
   if ((e = gemm(w.V1t, 1, w.Wt, 0, 1.f, 0.f, A, nullptr)) != cudaSuccess) return e;
+  // block-Jacobi sweeps: R^T in Qt's storage, A R kept transposed in Wt
+  {
+    const size_t smem = w.cplx ? SubShape<true>::bytes : SubShape<false>::bytes;
+    static bool attr[2] = {false, false};
+    if (!attr[w.cplx]) {
+      e = w.cplx ? cudaFuncSetAttribute(k_bj_sub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_bj_sub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr[w.cplx] = true;
+    }
+    const long items = count * (kNB / 2);
+    const long ctas = (items + kSubWarps - 1) / kSubWarps;
+    const int sgrid = (int)(ctas < 8L * big_grid() ? ctas : 8L * big_grid());
+    for (int sw = 0; sw < kBjSweeps; ++sw) {
+      for (int r = 0; r < kNB - 1; ++r) {
+        if (w.cplx)
+          k_bj_sub<true><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r);
+        else
+          k_bj_sub<false><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // B = A R (kept transposed in Wt); A <- R^H B written as (B^H R)^H; V1 <- V1 R.  All
+        // three multiply by the block rotation R on the right (tc_rot256: its nonzero blocks
+        // only).
+        auto rot = [&](const float* x, int cx, float* on, float* ot, int co) {
+          TcGemm g;
+          g.x = x;
+          g.y = w.Qt;
+          g.batch = count;
+          g.cplx = w.cplx;
+          g.conj_x = cx;
+          g.out_n = on;
+          g.out_t = ot;
+          g.conj_out = co;
+          g.round = r;
+          g.err = w.err;
+          return tc_rot256(g, s);
+        };
+        if ((e = rot(A, 0, nullptr, w.Wt, 0)) != cudaSuccess) return e;
+        if ((e = rot(w.Wt, 1, nullptr, A, 1)) != cudaSuccess) return e;
+        if ((e = rot(w.V1, 0, w.V1, w.V1t, 0)) != cudaSuccess) return e;
+      }
+    }
+  }
   // 4. Jacobi from Q = I with the first-order stop: M and Q^T
   const int grid = (int)(count < big_grid() ? count : big_grid());
   if (w.cplx)

@@ -86,6 +86,9 @@ WORKLOADS = {
     "tfim1d_L4_N1024": dict(lattice=(4096,), cluster=(4,), h=1.0, kind="tfim"),
     # 2-D square lattice 64 x 64, h = 3, 2 x 2 clusters (256 x 256 pair marginals), 32 x 32 clusters
     "tfim2d_L4_32x32": dict(lattice=(64, 64), cluster=(2, 2), h=3.0, kind="tfim"),
+    # the 4-spin-cluster chain at 1024 spins (256 clusters): a D = 256 case small enough for
+    # profiler captures (a few GB on the device)
+    "tfim1d_L4_N256": dict(lattice=(1024,), cluster=(4,), h=1.0, kind="tfim"),
 }
 
 
