@@ -407,9 +407,11 @@ __device__ void dk_matrix_herm(T* Ar, T* Ai, T* lam, int tid) {
 // Returns the number of sweeps performed.
 // With DK the sweeps may also stop early under dk_stop; *dk then tells the caller to
 // reconstruct with the first-order correction (dk_matrix) instead of diag(max(l, 0)).
+// nrm_min (squared Frobenius norm) raises the scale of the stopping test, for a principal block
+// whose accuracy is judged against the whole matrix it belongs to.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
 __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr,
-                          T* off_out = nullptr) {
+                          T* off_out = nullptr, T nrm_min = T(0)) {
   static_assert(n == 2 || n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   // blocks (GB) and eigenvector rows (GV) a thread loads before it stores any: a matrix staged
@@ -426,6 +428,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
     nrm += a * a;
   }
   nrm = gsum<NT>(nrm, red);
+  if (nrm < nrm_min) nrm = nrm_min;  // a block of a larger matrix: stop at that matrix's scale
   if constexpr (VEC && INIT_V) {
     for (int e = tid; e < n * n; e += NT) V[(e / n) * LD + (e % n)] = (e / n == e % n) ? T(1) : T(0);
   }
@@ -594,7 +597,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
 // Returns the number of sweeps performed.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
 __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, bool* dk = nullptr,
-                           T* off_out = nullptr) {
+                           T* off_out = nullptr, T nrm_min = T(0)) {
   static_assert(n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;  // as in jacobi_sym (measured)
@@ -605,6 +608,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, b
     nrm += Ar[o] * Ar[o] + Ai[o] * Ai[o];
   }
   nrm = gsum<NT>(nrm, red);
+  if (nrm < nrm_min) nrm = nrm_min;  // a block of a larger matrix: stop at that matrix's scale
   if constexpr (VEC && INIT_V) {
     for (int e = tid; e < n * n; e += NT) {
       const int o = (e / n) * LD + (e % n);

@@ -198,9 +198,28 @@ struct SubShape {
 
 __device__ __forceinline__ int kc4i(int r, int k) { return ((k >> 2) * kN + r) * 4 + (k & 3); }
 
+// ||A_b||_F^2 of every matrix (hi + lo), one CTA per matrix, fixed summation order.
+__global__ void __launch_bounds__(256) k_fro2(const float* __restrict__ A, int npl, float* __restrict__ out) {
+  __shared__ float red[8];
+  const float* a = A + (size_t)blockIdx.x * npl * kPl;
+  float s = 0.f;
+  for (int pl = 0; pl < npl; pl += 2)
+    for (int e = threadIdx.x; e < kPl; e += 256) {
+      const float v = a[pl * kPl + e] + a[(pl + 1) * kPl + e];
+      s = fmaf(v, v, s);
+    }
+  s = gsum<256>(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// fro2[b] = ||A_b||_F^2: a pair block stops at the accuracy the whole matrix needs.  The scalar
+// test off^2 <= (n u)^2 ||A||^2 over 120 block pairs of a sweep holds for the matrix when every
+// block meets off^2 <= (256 u)^2 ||A||^2 / 120, i.e. the block test (32 u)^2 nrm with
+// nrm >= (256 / 32)^2 / 120 ||A||^2 ~ 0.5 ||A||^2.
 template <bool CPLX>
 __global__ void __launch_bounds__(32 * kSubWarps)
-    k_bj_sub(const float* __restrict__ A, float* __restrict__ Rt, long count, int round) {
+    k_bj_sub(const float* __restrict__ A, float* __restrict__ Rt, long count, int round,
+             const float* __restrict__ fro2) {
   constexpr int NPL = CPLX ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -242,10 +261,11 @@ __global__ void __launch_bounds__(32 * kSubWarps)
       }
     }
     __syncwarp();
+    const float floor2 = 0.5f * fro2[b];
     if constexpr (CPLX)
-      jacobi_herm<float, kSub, kSLD, 32, true>(Sr, Si, Ur, Ui, cs, red, lane);
+      jacobi_herm<float, kSub, kSLD, 32, true>(Sr, Si, Ur, Ui, cs, red, lane, nullptr, nullptr, floor2);
     else
-      jacobi_sym<float, kSub, kSLD, 32, true>(Sr, Ur, cs, red, lane);
+      jacobi_sym<float, kSub, kSLD, 32, true>(Sr, Ur, cs, red, lane, nullptr, nullptr, floor2);
     // R^T on the pair's index set: R^T[g(j)][g(t)] = U[t][j].  tc_rot256 reads R^T only there
     // (the rows of the pair's column blocks at the pair's K slices), so the zeros elsewhere are
     // never written.  A lane writes one 4-index chunk of one row as a float4.
@@ -349,12 +369,15 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
     const long items = count * (kNB / 2);
     const long ctas = (items + kSubWarps - 1) / kSubWarps;
     const int sgrid = (int)(ctas < 8L * big_grid() ? ctas : 8L * big_grid());
+    float* fro2 = reinterpret_cast<float*>(w.M);  // M is free until the polish
+    k_fro2<<<(unsigned)count, 256, 0, s>>>(A, w.cplx ? 4 : 2, fro2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int sw = 0; sw < kBjSweeps; ++sw) {
       for (int r = 0; r < kNB - 1; ++r) {
         if (w.cplx)
-          k_bj_sub<true><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r);
+          k_bj_sub<true><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r, fro2);
         else
-          k_bj_sub<false><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r);
+          k_bj_sub<false><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r, fro2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // B = A R (kept transposed in Wt); A <- R^H B written as (B^H R)^H; V1 <- V1 R.  All
         // three multiply by the block rotation R on the right (tc_rot256: its nonzero blocks
@@ -375,7 +398,8 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
         };
         if ((e = rot(A, 0, nullptr, w.Wt, 0)) != cudaSuccess) return e;
         if ((e = rot(w.Wt, 1, nullptr, A, 1)) != cudaSuccess) return e;
-        if ((e = rot(w.V1, 0, w.V1, w.V1t, 0)) != cudaSuccess) return e;
+        // (V1^T is not read again in this projection: the steps after the sweeps use V1)
+        if ((e = rot(w.V1, 0, w.V1, nullptr, 0)) != cudaSuccess) return e;
       }
     }
   }
