@@ -486,16 +486,18 @@ def test_mixed_precision_reaches_the_float64_bound(ve):
     assert max(out.values()) <= mo.tfim_chain_jw_energy(32, 1.0, 1.0) / 32
 
 
-@pytest.mark.parametrize("lattice,cluster", [((64,), (2,)), ((16,), (4,))])
+@pytest.mark.parametrize("lattice,cluster", [((64,), (2,)), ((16,), (4,)), ((4, 6), (2, 2))])
 def test_mixed_sweeps_track_the_oracle(ve, lattice, cluster):
     """Mixed-precision sweeps (float32 arithmetic in the pair pass, the DFT and both
     projections; float64 state and reductions) stay within float32 rounding of the float64
     oracle: the whole state after 30 sweeps within 30 times the per-sweep bound of a float32
     projection, 8 (D + 16) 2^-24, relative (the sweep is nonexpansive, so errors add at most
-    linearly): 4.6e-4 at D = 16, 3.9e-3 at D = 256."""
-    pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 0.8, 1)))
+    linearly): 4.6e-4 at D = 16, 3.9e-3 at D = 256.  At D = 256 (a chain of 4-spin clusters and
+    a 2-D lattice of 2 x 2 clusters) the projections run on the tensor cores with block Jacobi."""
+    dim = len(lattice)
+    pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 0.8, dim)))
     st = vo.initial_state(pb)
-    h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 0.8),
+    h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(dim, 1.0, 0.8),
                      ve.ve_default_options(precision=1))
     try:
         ve.ve_iterate(h, 30, 0.0)
