@@ -318,6 +318,18 @@ int ve_circulant_project(const double* x_in, double* x_out, int dim, const int M
 int ve_circulant_project_noalloc(const double* x_in, double* x_out, int dim, const int M[2], int D,
                                  int precision, void* stream);
 
+/* ---- failure detection (the paper has no counterpart) ----------------------------------
+ * Every wait inside the tensor-core kernels (mbarrier phases of the TMA ring and of the tensor-
+ * memory accumulators) gives up after ~2 s of clock, sets an error word, drains the copies and
+ * products it issued, frees its tensor memory and returns; ve_iterate then reports VE_ETIMEOUT.
+ * ve_selftest_bounded_wait exercises that path on the current device without a fault: it runs
+ * one 256 x 256 tensor-core product whose loads are deliberately never issued, so its waits run
+ * out, then the same product normally.  Returns VE_OK when the first reported its timeout and
+ * the second ran clean on the same context; *seconds receives the first call's device time.
+ * Errors: VE_EINVAL, VE_ENOMEM, VE_ECUDA, VE_ETIMEOUT (a timeout went unreported, or a clean
+ * product reported one).  Takes ~2 s. */
+int ve_selftest_bounded_wait(double* seconds);
+
 /* ---- general Hamiltonians: Algorithm 5 (Sec. 3.2, "practical scheme") -------------------
  * No translation invariance: random fields, inhomogeneous or long-range couplings.  Every
  * cluster i has its own H_i and rho_i, every pair i < j its own H_ij, rho~_ij, Lambda_ij,

@@ -408,10 +408,12 @@ __device__ void dk_matrix_herm(T* Ar, T* Ai, T* lam, int tid) {
 // With DK the sweeps may also stop early under dk_stop; *dk then tells the caller to
 // reconstruct with the first-order correction (dk_matrix) instead of diag(max(l, 0)).
 // nrm_min (squared Frobenius norm) raises the scale of the stopping test, for a principal block
-// whose accuracy is judged against the whole matrix it belongs to.
+// whose accuracy is judged against the whole matrix it belongs to; max_sw caps the sweeps (an
+// inexact solve, for the sub-problems of a block method that a later solve completes).
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
 __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr,
-                          T* off_out = nullptr, T nrm_min = T(0)) {
+                          T* off_out = nullptr, T nrm_min = T(0),
+                          int max_sw = JacobiTol<T>::max_sweeps) {
   static_assert(n == 2 || n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   // blocks (GB) and eigenvector rows (GV) a thread loads before it stores any: a matrix staged
@@ -436,7 +438,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
   if constexpr (DK) *dk = false;
   T off_last = T(0);
   int sweep = 0;
-  for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
+  for (; sweep < max_sw; ++sweep) {
     T off = T(0);
     for (int e = tid; e < n * n; e += NT) {
       const int i = e / n, j = e % n;
@@ -578,7 +580,7 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
     }
   }
   if (off_out) {
-    if (sweep == JacobiTol<T>::max_sweeps) {  // the last sweep ran after the last test
+    if (sweep == max_sw) {  // the last sweep ran after the last test
       T off = T(0);
       for (int e = tid; e < n * n; e += NT) {
         const int i = e / n, j = e % n;
@@ -597,7 +599,8 @@ __device__ int jacobi_sym(T* A, T* V, T* cs, T* red, int tid, bool* dk = nullptr
 // Returns the number of sweeps performed.
 template <typename T, int n, int LD, int NT, bool VEC, bool INIT_V = true, bool DK = false>
 __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, bool* dk = nullptr,
-                           T* off_out = nullptr, T nrm_min = T(0)) {
+                           T* off_out = nullptr, T nrm_min = T(0),
+                           int max_sw = JacobiTol<T>::max_sweeps) {
   static_assert(n % 4 == 0, "the block ordering pairs n / 2 indices");
   constexpr int H = n / 2;
   constexpr int GB = n > 64 ? 2 : 1, GV = n > 64 ? 2 : 1;  // as in jacobi_sym (measured)
@@ -620,7 +623,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, b
   if constexpr (DK) *dk = false;
   T off_last = T(0);
   int sweep = 0;
-  for (; sweep < JacobiTol<T>::max_sweeps; ++sweep) {
+  for (; sweep < max_sw; ++sweep) {
     T off = T(0);
     for (int e = tid; e < n * n; e += NT) {
       const int i = e / n, j = e % n;
@@ -822,7 +825,7 @@ __device__ int jacobi_herm(T* Ar, T* Ai, T* Vr, T* Vi, T* cs, T* red, int tid, b
     }
   }
   if (off_out) {
-    if (sweep == JacobiTol<T>::max_sweeps) {  // the last sweep ran after the last test
+    if (sweep == max_sw) {  // the last sweep ran after the last test
       T off = T(0);
       for (int e = tid; e < n * n; e += NT) {
         const int i = e / n, j = e % n;

@@ -192,6 +192,9 @@ struct TcGemm {
   int* err = nullptr;
   int round = 0;     // tc_rot256: the block-Jacobi round
   int conj_out = 0;  // conjugate the result before writing it
+  // failure-detection test only (ve_selftest_bounded_wait): the loads are never issued, so the
+  // kernel's bounded waits run out and it must report *err = 1 and return
+  int withhold_loads = 0;
 };
 cudaError_t tc_gemm256(const TcGemm& g, cudaStream_t s);
 // Block Jacobi on 256 x 256 matrices: TC_BJ_NB blocks of TC_BJ_BS indices, paired by the circle
@@ -214,6 +217,8 @@ struct TcProjWs {
         *Wt = nullptr, *M = nullptr, *Qt = nullptr;
   unsigned char* jws = nullptr;  // Jacobi staging, one slice per CTA
   int* err = nullptr;            // device word: 1 after a tensor-core kernel gave up waiting
+  int bj_sweeps = 2;             // block-Jacobi sweeps per projection
+  int bj_inner = 1;              // Jacobi sweeps per block sub-problem (0: to convergence)
 };
 size_t tc_proj_ws_bytes(long cap, int cplx);
 int tc_proj_ws_init(TcProjWs& w, long cap, int cplx, void* mem, size_t bytes);

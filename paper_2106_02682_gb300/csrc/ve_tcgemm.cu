@@ -16,15 +16,17 @@
 // bytes each), and a thread reading one row's chunk as a float4 is coalesced with its
 // neighbours.
 //
-// Kernel: one CTA per SM, persistent over (matrix, half) tiles of 128 x 256 outputs.  Warp 0
-// issues the TMA loads of 16-wide K slices into a ring of stages, warp 1 allocates tensor memory
-// and issues the MMAs from one thread, warps 2-5 read the accumulators back (tcgen05.ld) and
-// write the split result, normal and/or transposed.  Every wait is bounded (ve_tc.cuh).
+// Kernel: one CTA per SM, persistent over (matrix, half, column group) tiles of 128 output rows.
+// Warp 0 issues the TMA loads of 16-wide K slices into a ring of stages, warp 1 allocates tensor
+// memory and issues the MMAs from one thread into one of two accumulators where they fit, and
+// warps 2-9 read the other accumulator back (tcgen05.ld) meanwhile and write the split result,
+// normal and/or transposed.  Every wait is bounded (ve_tc.cuh).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include "../../include/ve.h"
 #include "ve_internal.h"
 #include "ve_tc.cuh"
 
@@ -36,6 +38,12 @@ using namespace tc;
 
 // ROT: the right factor is a block rotation R (see tc_rot256): only the TC_BJ_BS-row slices of
 // y = R^T that hold a pair's blocks are loaded, two per stage; a stage's K slice is one block.
+//
+// A tile is (matrix, 128-row half, column group): NCG column groups of TN output columns.  Its
+// accumulator (re, and im when complex) takes ACC tensor-memory columns, and NBUF = 512 / ACC
+// accumulators are in flight, so that the epilogue of one tile overlaps the MMAs of the next.
+// A full product has one column group; a complex rotation has two (4 pairs, 8 column blocks
+// each), which makes its accumulator half as wide and lets it double-buffer too.
 template <bool CPLX, bool ROT = false>
 struct TcCfg {
   static constexpr int NPL = CPLX ? 4 : 2;            // planes of a split matrix
@@ -46,12 +54,20 @@ struct TcCfg {
   static constexpr int NYS = ROT ? 2 : 1;             // Y slices per plane and stage
   static constexpr int STAGE_BYTES = NPL * (XB + NYS * YB);
   static constexpr int STAGES = (CPLX && !ROT) ? 2 : 4;
-  static constexpr int TMEM_COLS = CPLX ? 512 : 256;  // re and im accumulators, 256 columns each
-  static constexpr int XSTAGE = 4 * 32 * 17 * 4;   // epilogue transpose staging, 32 x 16 per warp
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + XSTAGE;  // + align, barriers
+  static constexpr int NCG = (ROT && CPLX) ? 2 : 1;   // column groups per (matrix, half)
+  static constexpr int TN = 256 / NCG;                // output columns of a tile
+  static constexpr int ACC = (CPLX ? 2 : 1) * TN;     // tensor-memory columns of one accumulator
+  static constexpr int NBUF = 512 / ACC >= 2 ? 2 : 1;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int KSTEPS = ROT ? 2 * (TC_BJ_NB / 2) / NCG : 256 / KS;  // stages per tile
+  static constexpr int EPI_WARPS = 8;
+  static constexpr int XSTAGE = EPI_WARPS * 32 * 17 * 4;  // epilogue transpose staging, 32 x 16 per warp
+  // one CTA per SM: it holds all 512 tensor-memory columns
+  static constexpr size_t SMEM_USED = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + XSTAGE;
+  static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
 };
 
-constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kPlane = 256 * 256;
 
 struct TcParams {
@@ -59,6 +75,7 @@ struct TcParams {
   int conj_x, conj_y;
   int round;     // ROT: the block-Jacobi round whose pairs R rotates
   int conj_out;  // conjugate the result before it is written
+  int withhold;  // failure-detection test: issue no loads, so every wait runs out
   float alpha, beta;
   float* out_n;
   float* out_t;
@@ -83,6 +100,20 @@ __device__ __forceinline__ void block_pair(int r, int k, int& p, int& q) {
   q = a < b ? b : a;
 }
 
+// Output column block of accumulator slot `slot` (16 columns) of column group cg.  Full product:
+// the slots are the blocks in order.  ROT: slot 2 j + w of group cg is block p (w = 0) or q (w =
+// 1) of pair cg * (pairs per group) + j.
+template <bool ROT, int NCG>
+__device__ __forceinline__ int slot_block(int round, int cg, int slot) {
+  if constexpr (!ROT) {
+    return slot;
+  } else {
+    int bp, bq;
+    block_pair(round, cg * (TC_BJ_NB / 2 / NCG) + (slot >> 1), bp, bq);
+    return (slot & 1) ? bq : bp;
+  }
+}
+
 template <bool CPLX, bool ROT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tcgemm(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap my, const TcParams p) {
@@ -91,23 +122,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + C::STAGES * C::STAGE_BYTES);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* tfull = empty + C::STAGES;
-  uint64_t* tempty = tfull + 1;
-  uint64_t* drain = tempty + 1;
+  uint64_t* tfull = empty + C::STAGES;  // [NBUF]
+  uint64_t* tempty = tfull + 2;         // [NBUF]
+  uint64_t* drain = tempty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   float* xst = reinterpret_cast<float*>(base + C::STAGES * C::STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long ntiles = 2 * p.batch;
+  const long ntiles = 2L * C::NCG * p.batch;
+  // tile t: matrix t / (2 NCG), row half (t / NCG) & 1, column group t % NCG
+  auto tile = [&](long t, int& b, int& h, int& cg) {
+    b = (int)(t / (2 * C::NCG));
+    h = (int)((t / C::NCG) & 1);
+    cg = (int)(t % C::NCG);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(tfull, 1);
-    mbar_init(tempty, 4);  // one arrival per epilogue warp
+    for (int i = 0; i < C::NBUF; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], C::EPI_WARPS);  // one arrival per epilogue warp
+    }
     mbar_init(drain, 1);
     *abort = 0;
     fence_barrier_init();
@@ -129,19 +168,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       int s = 0;
       uint32_t ph = 0;
       uint32_t issued = 0, iph = 0;  // per stage: a load was issued, and the phase it completes
-      for (long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
-        const int b = (int)(t >> 1), h = (int)(t & 1);
-        for (int kb = 0; kb < 256 / C::KS; ++kb) {
+      for (long t = blockIdx.x; t < ntiles && !*abort && !p.withhold; t += gridDim.x) {
+        int b, h, cg;
+        tile(t, b, h, cg);
+        for (int kb = 0; kb < C::KSTEPS; ++kb) {
           if (!mbar_wait(&empty[s], ph ^ 1, abort)) break;
           issued |= 1u << s;
           iph = (iph & ~(1u << s)) | (ph << s);
           mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
           unsigned char* st = base + s * C::STAGE_BYTES;
-          // K slice of this stage; ROT: stage kb is block (kb & 1 ? q : p) of pair kb / 2
+          // K slice of this stage; ROT: stage kb is block (kb & 1 ? q : p) of the group's pair kb / 2
           static_assert(!ROT || TC_BJ_BS == C::KS, "a rotation stage spans one block");
           int kslice = kb, bp = 0, bq = 0;
           if constexpr (ROT) {
-            block_pair(p.round, kb >> 1, bp, bq);
+            block_pair(p.round, cg * (TC_BJ_NB / 2 / C::NCG) + (kb >> 1), bp, bq);
             kslice = (kb & 1) ? bq : bp;
           }
           for (int pl = 0; pl < C::NPL; ++pl) {
@@ -183,10 +223,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t ph = 0;
       int local = 0;
       for (long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++local) {
-        if (!mbar_wait(tempty, (local & 1) ^ 1, abort)) break;
+        const int bi = local % C::NBUF;
+        const uint32_t use = (uint32_t)(local / C::NBUF);  // earlier uses of this accumulator
+        if (!mbar_wait(&tempty[bi], (use & 1) ^ 1, abort)) break;
         tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(bi * C::ACC);
         bool ok = true;
-        for (int kb = 0; kb < 256 / C::KS; ++kb) {
+        for (int kb = 0; kb < C::KSTEPS; ++kb) {
           if (!mbar_wait(&full[s], ph, abort)) {
             ok = false;
             break;
@@ -194,21 +237,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t st = smem_u32(base + s * C::STAGE_BYTES);
           const uint32_t xs = st, ys0 = st + C::NPL * C::XB;
-          // ROT: the stage's K slice feeds the output columns of both blocks of its pair, each
+          // ROT: the stage's K slice feeds the accumulator slots of both blocks of its pair, each
           // accumulated only over the pair's 2 stages (R is zero elsewhere): N = TC_BJ_BS
-          int bp = 0, bq = 0;
-          if constexpr (ROT) block_pair(p.round, kb >> 1, bp, bq);
 #pragma unroll
           for (int cb = 0; cb < C::NYS; ++cb) {
             const uint32_t ys = ys0 + cb * C::NPL * C::YB;
-            const uint32_t c0 = ROT ? (uint32_t)TC_BJ_BS * (uint32_t)(cb ? bq : bp) : 0u;
+            const uint32_t c0 = ROT ? (uint32_t)TC_BJ_BS * (uint32_t)(2 * (kb >> 1) + cb) : 0u;
             constexpr int NN = ROT ? TC_BJ_BS : 256;
 #pragma unroll
             for (int ks = 0; ks < C::KS / 8; ++ks) {
               auto mma = [&](int xp, int yp, uint32_t col, int neg, bool first) {
                 const uint64_t ad = smem_desc(xs + xp * C::XB + ks * 2 * XLBO, XLBO, SBO);
                 const uint64_t bd = smem_desc(ys + yp * C::YB + ks * 2 * YLBO, YLBO, SBO);
-                mma_tf32(tmem + c0 + col, ad, bd, idesc_tf32(128, NN, neg, 0), first ? 0u : 1u);
+                mma_tf32(acc + c0 + col, ad, bd, idesc_tf32(128, NN, neg, 0), first ? 0u : 1u);
               };
               const bool f0 = (ROT ? (kb & 1) == 0 : kb == 0) && ks == 0;
               if constexpr (!CPLX) {
@@ -224,12 +265,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma(2, 3, 0, nr, false);
                 mma(3, 2, 0, nr, false);
                 const int ni1 = sy < 0 ? 1 : 0, ni2 = sx < 0 ? 1 : 0;
-                mma(0, 2, 256, ni1, f0);
-                mma(0, 3, 256, ni1, false);
-                mma(1, 2, 256, ni1, false);
-                mma(2, 0, 256, ni2, false);
-                mma(2, 1, 256, ni2, false);
-                mma(3, 0, 256, ni2, false);
+                mma(0, 2, C::TN, ni1, f0);
+                mma(0, 3, C::TN, ni1, false);
+                mma(1, 2, C::TN, ni1, false);
+                mma(2, 0, C::TN, ni2, false);
+                mma(2, 1, C::TN, ni2, false);
+                mma(3, 0, C::TN, ni2, false);
               }
             }
           }
@@ -240,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!ok) break;
-        mma_commit(tfull);
+        mma_commit(&tfull[bi]);
       }
       if (*abort) {
         // every MMA issued so far completes before this commit's arrival
@@ -250,23 +291,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) ... + 31, i.e. output rows
-    const int q = warp & 3;
+    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) ... + 31, i.e. output rows, and
+    // the accumulator slots of its parity (w - 2) / 4
+    const int q = warp & 3, half = (warp - 2) >> 2;
     const int m = 32 * q + lane;
+    float* tile_st = xst + (warp - 2) * (32 * 17);
     int local = 0;
     for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
-      const int b = (int)(t >> 1), h = (int)(t & 1);
+      int b, h, cg;
+      tile(t, b, h, cg);
+      const int bi = local % C::NBUF;
+      const uint32_t use = (uint32_t)(local / C::NBUF);
       // warp-uniform decision: the tensor-memory loads below are .sync.aligned
-      const bool ok = !*abort && mbar_wait(tfull, local & 1, abort);
+      const bool ok = !*abort && mbar_wait(&tfull[bi], use & 1, abort);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
+      const uint32_t acc = tmem + (uint32_t)(bi * C::ACC) + ((uint32_t)(32 * q) << 16);
       const int gr = 128 * h + m;  // output row
       float* on = p.out_n ? p.out_n + (size_t)b * C::NPL * kPlane : nullptr;
       float* ot = p.out_t ? p.out_t + (size_t)b * C::NPL * kPlane : nullptr;
-      for (int n0 = 0; n0 < 256; n0 += 16) {
+      for (int slot = half; slot < C::TN / 16; slot += 2) {
+        const int n0 = 16 * slot_block<ROT, C::NCG>(p.round, cg, slot);  // output column
         float vr[16], vi[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + n0, vr);
-        if constexpr (CPLX) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 256 + n0, vi);
+        tmem_ld16(acc + 16 * slot, vr);
+        if constexpr (CPLX) tmem_ld16(acc + C::TN + 16 * slot, vi);
         const float ci = p.conj_out ? -p.alpha : p.alpha;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -307,7 +355,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           // columns n0 .. n0 + 15; in D^T's KC4 layout a 4-row chunk of one column is one float4,
           // and the 16 columns of a chunk are 256 contiguous bytes, so each half-warp stores one
           // chunk row in one contiguous segment.
-          float* tile = xst + q * (32 * 17);
           const int gr0 = 128 * h + 32 * q;
 #pragma unroll
           for (int part = 0; part < (CPLX ? 4 : 2); ++part) {
@@ -315,14 +362,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const float hv = tf32_hi(v[j]);
-              tile[lane * 17 + j] = (part & 1) ? v[j] - hv : hv;
+              tile_st[lane * 17 + j] = (part & 1) ? v[j] - hv : hv;
             }
             __syncwarp();
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
               const int qq = lane + 32 * i, c = qq >> 4, n = qq & 15;
-              const float4 w4 = make_float4(tile[(4 * c) * 17 + n], tile[(4 * c + 1) * 17 + n],
-                                            tile[(4 * c + 2) * 17 + n], tile[(4 * c + 3) * 17 + n]);
+              const float4 w4 = make_float4(tile_st[(4 * c) * 17 + n], tile_st[(4 * c + 1) * 17 + n],
+                                            tile_st[(4 * c + 2) * 17 + n], tile_st[(4 * c + 3) * 17 + n]);
               *reinterpret_cast<float4*>(ot + part * kPlane + ((gr0 / 4 + c) * 256 + n0 + n) * 4) = w4;
             }
             __syncwarp();
@@ -331,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty);
+      if (lane == 0) mbar_arrive(&tempty[bi]);
     }
   }
 
@@ -400,12 +447,13 @@ cudaError_t launch(const TcGemm& g, cudaStream_t s) {
   p.conj_y = g.conj_y;
   p.round = g.round;
   p.conj_out = g.conj_out;
+  p.withhold = g.withhold_loads;
   p.alpha = g.alpha;
   p.beta = g.beta;
   p.out_n = g.out_n;
   p.out_t = g.out_t;
   p.err = g.err;
-  const long tiles = 2 * g.batch;
+  const long tiles = 2L * C::NCG * g.batch;
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
   k_tcgemm<CPLX, ROT><<<grid, kThreads, C::SMEM, s>>>(mx, my, p);
   return cudaGetLastError();
@@ -431,3 +479,54 @@ cudaError_t tc_rot256(const TcGemm& g, cudaStream_t s) {
 }
 
 }  // namespace ve
+
+// ---------------------------------------------------------------- failure-detection self-test
+extern "C" int ve_selftest_bounded_wait(double* seconds) {
+  using namespace ve;
+  if (!seconds) return VE_EINVAL;
+  cudaGetLastError();
+  const size_t mat = (size_t)2 * kPlane * sizeof(float);  // one real split matrix
+  float* buf = nullptr;
+  int* err = nullptr;
+  if (cudaMalloc(&buf, 3 * mat) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (buf) cudaFree(buf);
+    return VE_ENOMEM;
+  }
+  int rc = VE_OK;
+  int h_err = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TcGemm g;
+  g.x = buf;
+  g.y = buf + 2 * kPlane;
+  g.out_n = buf + 4 * kPlane;
+  g.batch = 1;
+  g.err = err;
+  float ms = 0.f;
+  bool ok = cudaMemset(buf, 0, 3 * mat) == cudaSuccess && cudaMemset(err, 0, sizeof(int)) == cudaSuccess &&
+            cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  // 1. loads withheld: the waits must run out, the kernel report it and return
+  g.withhold_loads = 1;
+  ok = ok && cudaEventRecord(e0, 0) == cudaSuccess && tc_gemm256(g, 0) == cudaSuccess &&
+       cudaEventRecord(e1, 0) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+       cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+       cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (!ok) rc = VE_ECUDA;
+  else if (h_err != 1) rc = VE_ETIMEOUT;  // the stall went unreported
+  // 2. the context is still usable: the same product with its loads runs clean
+  if (rc == VE_OK) {
+    g.withhold_loads = 0;
+    h_err = 0;
+    ok = cudaMemset(err, 0, sizeof(int)) == cudaSuccess && tc_gemm256(g, 0) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess &&
+         cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) rc = VE_ECUDA;
+    else if (h_err != 0) rc = VE_ETIMEOUT;
+  }
+  *seconds = ms * 1e-3;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  cudaFree(err);
+  return rc;
+}

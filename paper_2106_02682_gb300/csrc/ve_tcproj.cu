@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(kNT, 1)
 // R's nonzero blocks (tc_rot256), so only those blocks of R^T are ever written.  A sweep of rounds annihilates every off-diagonal
 // block once; like scalar Jacobi it converges quadratically.
 constexpr int kBS = TC_BJ_BS, kNB = TC_BJ_NB, kSub = 2 * kBS, kSLD = kSub + 1, kSubWarps = 4;
-constexpr int kBjSweeps = 2;
 
 template <bool CPLX>
 struct SubShape {
@@ -219,7 +218,7 @@ __global__ void __launch_bounds__(256) k_fro2(const float* __restrict__ A, int n
 template <bool CPLX>
 __global__ void __launch_bounds__(32 * kSubWarps)
     k_bj_sub(const float* __restrict__ A, float* __restrict__ Rt, long count, int round,
-             const float* __restrict__ fro2) {
+             const float* __restrict__ fro2, int max_inner) {
   constexpr int NPL = CPLX ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -263,9 +262,10 @@ __global__ void __launch_bounds__(32 * kSubWarps)
     __syncwarp();
     const float floor2 = 0.5f * fro2[b];
     if constexpr (CPLX)
-      jacobi_herm<float, kSub, kSLD, 32, true>(Sr, Si, Ur, Ui, cs, red, lane, nullptr, nullptr, floor2);
+      jacobi_herm<float, kSub, kSLD, 32, true>(Sr, Si, Ur, Ui, cs, red, lane, nullptr, nullptr, floor2,
+                                               max_inner);
     else
-      jacobi_sym<float, kSub, kSLD, 32, true>(Sr, Ur, cs, red, lane, nullptr, nullptr, floor2);
+      jacobi_sym<float, kSub, kSLD, 32, true>(Sr, Ur, cs, red, lane, nullptr, nullptr, floor2, max_inner);
     // R^T on the pair's index set: R^T[g(j)][g(t)] = U[t][j].  tc_rot256 reads R^T only there
     // (the rows of the pair's column blocks at the pair's K slices), so the zeros elsewhere are
     // never written.  A lane writes one 4-index chunk of one row as a float4.
@@ -372,12 +372,19 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
     float* fro2 = reinterpret_cast<float*>(w.M);  // M is free until the polish
     k_fro2<<<(unsigned)count, 256, 0, s>>>(A, w.cplx ? 4 : 2, fro2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    for (int sw = 0; sw < kBjSweeps; ++sw) {
+    // Two block sweeps, each sub-problem one Jacobi sweep (an inexact block solve: the polish
+    // below completes the eigensolve to the full tolerance).  Measured in steady state on the
+    // 4-spin-cluster chain and the 2-D lattice: one block sweep leaves the scalar polish 1.2
+    // sweeps per wavevector block (far dearer than a second block sweep), a third block sweep
+    // costs more than the polish it saves, and sub-problems solved to convergence instead of one
+    // sweep cost 3-4 % more time for the same polish work.
+    const int inner = w.bj_inner > 0 ? w.bj_inner : JacobiTol<float>::max_sweeps;
+    for (int sw = 0; sw < w.bj_sweeps; ++sw) {
       for (int r = 0; r < kNB - 1; ++r) {
         if (w.cplx)
-          k_bj_sub<true><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r, fro2);
+          k_bj_sub<true><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r, fro2, inner);
         else
-          k_bj_sub<false><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r, fro2);
+          k_bj_sub<false><<<sgrid, 32 * kSubWarps, smem, s>>>(A, w.Qt, count, r, fro2, inner);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // B = A R (kept transposed in Wt); A <- R^H B written as (B^H R)^H; V1 <- V1 R.  All
         // three multiply by the block rotation R on the right (tc_rot256: its nonzero blocks

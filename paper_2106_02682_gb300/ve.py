@@ -115,6 +115,7 @@ def _load():
         "ve_profile_read": (c_int, [H, P_double, ctypes.POINTER(c_long)]),
         "ve_profile_sweeps": (c_int, [H, P_double, P_double]),
         "ve_profile_first_order": (c_int, [H, ctypes.POINTER(c_long), ctypes.POINTER(c_long)]),
+        "ve_selftest_bounded_wait": (c_int, [P_double]),
         "ve_create_batch": (c_int, [c_int, ctypes.POINTER(ve_lattice), ctypes.POINTER(ve_cluster),
                                     ctypes.POINTER(ve_hamiltonian), ctypes.POINTER(ve_options),
                                     ctypes.POINTER(c_void_p)]),
@@ -312,6 +313,14 @@ def ve_profile_first_order(h):
     p, k = (c_long * 2)(), (c_long * 2)()
     _check(_lib.ve_profile_first_order(c_void_p(h), p, k), "ve_profile_first_order")
     return (p[0], p[1]), (k[0], k[1])
+
+
+def ve_selftest_bounded_wait():
+    """Run the tensor-core kernels' timeout path once (loads withheld, then a clean call);
+    returns the stalled call's device seconds.  Raises VEError on failure."""
+    sec = c_double()
+    _check(_lib.ve_selftest_bounded_wait(ctypes.byref(sec)), "ve_selftest_bounded_wait")
+    return sec.value
 
 
 def ve_project_psd_sym(in_ptr, out_ptr, n, count, precision=VE_PREC_FP64, stream=None):

@@ -456,6 +456,14 @@ def test_nonfinite_state_is_reported(ve):
         ve.ve_destroy(h)
 
 
+def test_tensor_core_waits_time_out_cleanly(ve):
+    """Failure detection without a GPU fault: a tensor-core product whose loads are withheld must
+    see its bounded waits run out, report the timeout and return within a few seconds (not
+    hang), and the same context must then run the product cleanly."""
+    sec = ve.ve_selftest_bounded_wait()
+    assert 0.5 < sec < 10.0, sec
+
+
 def test_converges_to_the_paper_table_value(ve):
     """TFI 20x1, 2x1 clusters, h = 1 (Sec. 4 table): 10 000 sweeps on the GPU."""
     h = ve.ve_create((20,), (2,), ve.ve_ham_tfim(1, 1.0, 1.0))
