@@ -243,23 +243,25 @@ __global__ void __launch_bounds__(1024) k_dense_weyl_min(const double* B, int n,
 }
 
 // C (M x N) = op(A) diag(s) op(B), op(A)(i,k) = TA ? A[k][i] : A[i][k], op(B)(k,j) = TB ? B[j][k] :
-// B[k][j], s_k = max(scale[k], 0) (scale null: 1).  32 x 32 tiles, 64 threads with 4 x 4 outputs
-// each; float64 FMAs bound it (the part's float64 rate is ~2 FMA per SM clock), so the simple
-// shared-memory tiling suffices.
-template <bool TA, bool TB>
+// B[k][j], s_k = max(scale[k], 0) (scale null: 1).  BS x BS tiles, 64 threads with
+// (BS/8) x (BS/8) outputs each; float64 FMAs bound it (the part's float64 rate is ~2 FMA per SM
+// clock), so the simple shared-memory tiling suffices, and products too small to give every SM a
+// 32 x 32 tile take 16 x 16 tiles (n = 160: 100 CTAs instead of 25).  Every output sums its K
+// terms in the same order whatever the tile, so the results do not depend on it.
+template <bool TA, bool TB, int BS>
 __global__ void __launch_bounds__(64) k_gemm(int M, int N, int K, const double* __restrict__ A, int lda,
                                              const double* __restrict__ B, int ldb, double* __restrict__ C,
                                              int ldc, const double* __restrict__ scale) {
-  constexpr int BM = 32, BN = 32, BK = 16;
+  constexpr int BM = BS, BN = BS, BK = 16, TT = BS / 8;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-  double acc[4][4];
+  double acc[TT][TT];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < TT; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < TT; ++v) acc[u][v] = 0.0;
   for (int k0 = 0; k0 < K; k0 += BK) {
     for (int l = threadIdx.x; l < BM * BK; l += 64) {
       int ii, kk;
@@ -295,25 +297,25 @@ __global__ void __launch_bounds__(64) k_gemm(int M, int N, int K, const double* 
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[TT], b[TT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+      for (int u = 0; u < TT; ++u) a[u] = As[kk][ty * TT + u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
+      for (int v = 0; v < TT; ++v) b[v] = Bs[kk][tx * TT + v];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < TT; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < TT; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int gi = i0 + ty * 4 + u;
+  for (int u = 0; u < TT; ++u) {
+    const int gi = i0 + ty * TT + u;
     if (gi >= M) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int gj = j0 + tx * 4 + v;
+    for (int v = 0; v < TT; ++v) {
+      const int gj = j0 + tx * TT + v;
       if (gj < N) C[(size_t)gi * ldc + gj] = acc[u][v];
     }
   }
@@ -322,8 +324,13 @@ __global__ void __launch_bounds__(64) k_gemm(int M, int N, int K, const double* 
 template <bool TA, bool TB>
 cudaError_t gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                  int ldc, const double* scale, cudaStream_t s) {
-  const dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32));
-  k_gemm<TA, TB><<<grid, 64, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, scale);
+  if ((long)((M + 31) / 32) * ((N + 31) / 32) < 152) {
+    const dim3 grid((unsigned)((N + 15) / 16), (unsigned)((M + 15) / 16));
+    k_gemm<TA, TB, 16><<<grid, 64, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, scale);
+  } else {
+    const dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32));
+    k_gemm<TA, TB, 32><<<grid, 64, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, scale);
+  }
   return cudaGetLastError();
 }
 

@@ -42,6 +42,24 @@ def test_gpu_network_matches_the_reference(ve, n_in, hidden, layers, n_out, n):
         ve.ve_mlp_destroy(m)
 
 
+def test_training_is_reproducible_bit_for_bit(ve):
+    """Two networks from the same seed trained on the same data end with identical parameters
+    and loss: the training reductions have a fixed order (no atomics)."""
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(24, 1)).astype(np.float32)
+    t = rng.normal(size=(24, 8)).astype(np.float32)
+    out = []
+    for _ in range(2):
+        m = ve.ve_mlp_create(1, 64, 3, 8, 5)
+        try:
+            loss = ve.ve_mlp_train(m, x, t, 300, 1e-3)
+            out.append((loss, ve.ve_mlp_get_params(m).copy()))
+        finally:
+            ve.ve_mlp_destroy(m)
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 LATTICE, CLUSTER = (40,), (2,)
 
 
