@@ -12,6 +12,8 @@ bound of a mixed solve is held to 1e-6 per spin.  Double-float results (VE_PREC_
 to the float64 tolerances times 2^(53-48) = 32, the ratio of the two unit roundoffs; after 30
 sweeps the measured state error is 5-13x that of float64 mode (at most 6.2e-10, D = 256).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -517,6 +519,33 @@ def test_mixed_sweeps_track_the_oracle(ve, lattice, cluster):
         assert abs(cert.bound_per_spin - vo.certified_bound(pb, st)['bound_per_spin']) < 1e-3
     finally:
         ve.ve_destroy(h)
+
+
+def test_full_size_4spin_chain_mixed_matches_oracle(ve):
+    """The 4-spin-cluster benchmark chain itself (4096 spins, 1024 clusters, D = 256: 513
+    canonical wavevector blocks and 512 pair blocks per projection batch) in mixed precision, the
+    tensor-core path as the benchmark runs it (captured sweep graph after the first sweep), two
+    sweeps from the cold start against the float64 oracle over the whole state: within twice the
+    per-sweep float32 bound of the test above, and the certificate within 1e-3 per spin."""
+    lattice, cluster = (4096,), (4,)
+    vo.set_threads(os.cpu_count() or 1)
+    try:
+        pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 1.0, 1)))
+        st = vo.initial_state(pb)
+        h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 1.0),
+                         ve.ve_default_options(precision=1))
+        try:
+            ve.ve_iterate(h, 2, 0.0)
+            for _ in range(2):
+                vo.iterate(pb, st)
+            err = relerr(ve.ve_get_state(h), vo.pack_state(pb, st))
+            assert err < 2 * 8 * (pb.D + 16) * 2.0 ** -24, err
+            cert = ve.ve_bound(h)
+            assert abs(cert.bound_per_spin - vo.certified_bound(pb, st)['bound_per_spin']) < 1e-3
+        finally:
+            ve.ve_destroy(h)
+    finally:
+        vo.set_threads(1)
 
 
 # ------------------------------------------------------------------ batches of instances
