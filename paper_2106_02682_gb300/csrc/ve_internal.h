@@ -192,6 +192,9 @@ struct TcGemm {
   int* err = nullptr;
   int round = 0;     // tc_rot256: the block-Jacobi round
   int conj_out = 0;  // conjugate the result before writing it
+  // "plain" outputs: out_n / out_t written as float32 planes (re; re, im when complex) in the KC4
+  // layout, half the bytes of the split form; tc_rot256 always takes its x operand plain
+  int plain_n = 0, plain_t = 0;
   // failure-detection test only (ve_selftest_bounded_wait): the loads are never issued, so the
   // kernel's bounded waits run out and it must report *err = 1 and return
   int withhold_loads = 0;
@@ -201,8 +204,10 @@ cudaError_t tc_gemm256(const TcGemm& g, cudaStream_t s);
 // ordering (rr_pair(TC_BJ_NB, round, k)), TC_BJ_NB - 1 rounds a sweep.
 constexpr int TC_BJ_BS = 16, TC_BJ_NB = 256 / TC_BJ_BS;
 // x_b R_b for a block rotation R of round g.round, R nonzero only on each pair's 2 TC_BJ_BS square
-// block.  g.y holds R^T; only its pairs' row slices are read, and each output column block
-// accumulates over its pair's indices: 2 TC_BJ_BS / 256 of the products of tc_gemm256.
+// block.  g.y holds R^T (split); only its pairs' row slices are read, and each output column block
+// accumulates over its pair's indices: 2 TC_BJ_BS / 256 of the products of tc_gemm256.  g.x is
+// plain (split inside the kernel: the rotations move their whole operand for 1/8 of a product's
+// MMAs, so its bytes are the cost).
 cudaError_t tc_rot256(const TcGemm& g, cudaStream_t s);
 
 // Batched float32 PSD projection of 256 x 256 matrices with the products on the tensor cores

@@ -44,16 +44,24 @@ using namespace tc;
 // accumulators are in flight, so that the epilogue of one tile overlaps the MMAs of the next.
 // A full product has one column group; a complex rotation has two (4 pairs, 8 column blocks
 // each), which makes its accumulator half as wide and lets it double-buffer too.
+//
+// RAW (the rotations): x arrives plain -- NPX float32 planes, re (and im) -- and four converter
+// warps split each landed K slice into the hi / lo planes the MMAs read, in shared memory.  A
+// stage then holds [split x | y | raw x]; the TMA fills y and raw x, the converters split x.
 template <bool CPLX, bool ROT = false>
 struct TcCfg {
   static constexpr int NPL = CPLX ? 4 : 2;            // planes of a split matrix
+  static constexpr int NPX = CPLX ? 2 : 1;            // planes of a plain matrix
+  static constexpr bool RAW = ROT;                    // x plain, split in the kernel
   static constexpr int KS = 16;                       // K elements per stage
   static constexpr int XB = 128 * KS * 4;             // bytes of one X plane slice (128 rows)
   static constexpr int YR = ROT ? TC_BJ_BS : 256;     // rows of one Y plane slice
   static constexpr int YB = YR * KS * 4;              // bytes of one Y plane slice
   static constexpr int NYS = ROT ? 2 : 1;             // Y slices per plane and stage
-  static constexpr int STAGE_BYTES = NPL * (XB + NYS * YB);
-  static constexpr int STAGES = (CPLX && !ROT) ? 2 : 4;
+  static constexpr int RAWOFF = NPL * (XB + NYS * YB);  // raw x within a stage
+  static constexpr int STAGE_BYTES = RAWOFF + (RAW ? NPX * XB : 0);
+  static constexpr int TX_BYTES = (RAW ? NPX : NPL) * XB + NPL * NYS * YB;  // loaded by the TMA
+  static constexpr int STAGES = RAW ? (CPLX ? 3 : 4) : (CPLX ? 2 : 4);
   static constexpr int NCG = (ROT && CPLX) ? 2 : 1;   // column groups per (matrix, half)
   static constexpr int TN = 256 / NCG;                // output columns of a tile
   static constexpr int ACC = (CPLX ? 2 : 1) * TN;     // tensor-memory columns of one accumulator
@@ -61,13 +69,15 @@ struct TcCfg {
   static constexpr int TMEM_COLS = 512;
   static constexpr int KSTEPS = ROT ? 2 * (TC_BJ_NB / 2) / NCG : 256 / KS;  // stages per tile
   static constexpr int EPI_WARPS = 8;
+  static constexpr int CVT_WARPS = RAW ? 4 : 0;
+  static constexpr int THREADS = 32 * (2 + EPI_WARPS + CVT_WARPS);
   static constexpr int XSTAGE = EPI_WARPS * 32 * 17 * 4;  // epilogue transpose staging, 32 x 16 per warp
   // one CTA per SM: it holds all 512 tensor-memory columns
   static constexpr size_t SMEM_USED = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + XSTAGE;
   static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
 };
 
-constexpr int kThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kMaxThreads = 448;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue, (RAW) 10-13 converters
 constexpr int kPlane = 256 * 256;
 
 struct TcParams {
@@ -76,6 +86,7 @@ struct TcParams {
   int round;     // ROT: the block-Jacobi round whose pairs R rotates
   int conj_out;  // conjugate the result before it is written
   int withhold;  // failure-detection test: issue no loads, so every wait runs out
+  int plain_n, plain_t;  // write out_n / out_t as plain float32 planes (no hi / lo split)
   float alpha, beta;
   float* out_n;
   float* out_t;
@@ -115,14 +126,15 @@ __device__ __forceinline__ int slot_block(int round, int cg, int slot) {
 }
 
 template <bool CPLX, bool ROT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 1)
     k_tcgemm(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap my, const TcParams p) {
   using C = TcCfg<CPLX, ROT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + C::STAGES * C::STAGE_BYTES);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* tfull = empty + C::STAGES;  // [NBUF]
+  uint64_t* cvt = empty + C::STAGES;    // RAW: the stage's x is split
+  uint64_t* tfull = cvt + C::STAGES;    // [NBUF]
   uint64_t* tempty = tfull + 2;         // [NBUF]
   uint64_t* drain = tempty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
@@ -142,6 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&cvt[s], C::CVT_WARPS > 0 ? C::CVT_WARPS : 1);
     }
     for (int i = 0; i < C::NBUF; ++i) {
       mbar_init(&tfull[i], 1);
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(&empty[s], ph ^ 1, abort)) break;
           issued |= 1u << s;
           iph = (iph & ~(1u << s)) | (ph << s);
-          mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+          mbar_arrive_expect_tx(&full[s], C::TX_BYTES);
           unsigned char* st = base + s * C::STAGE_BYTES;
           // K slice of this stage; ROT: stage kb is block (kb & 1 ? q : p) of the group's pair kb / 2
           static_assert(!ROT || TC_BJ_BS == C::KS, "a rotation stage spans one block");
@@ -184,8 +197,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             block_pair(p.round, cg * (TC_BJ_NB / 2 / C::NCG) + (kb >> 1), bp, bq);
             kslice = (kb & 1) ? bq : bp;
           }
+          if constexpr (C::RAW) {
+            for (int pl = 0; pl < C::NPX; ++pl)
+              tma_load_4d(st + C::RAWOFF + pl * C::XB, &mx, &full[s], 0, 128 * h, kslice * (C::KS / 4),
+                          b * C::NPX + pl);
+          }
           for (int pl = 0; pl < C::NPL; ++pl) {
-            tma_load_4d(st + pl * C::XB, &mx, &full[s], 0, 128 * h, kslice * (C::KS / 4), b * C::NPL + pl);
+            if constexpr (!C::RAW)
+              tma_load_4d(st + pl * C::XB, &mx, &full[s], 0, 128 * h, kslice * (C::KS / 4), b * C::NPL + pl);
             if constexpr (ROT) {
               // the rows of R^T (columns of R) in the pair's two blocks
               tma_load_4d(st + C::NPL * C::XB + (0 * C::NPL + pl) * C::YB, &my, &full[s], 0,
@@ -230,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t acc = tmem + (uint32_t)(bi * C::ACC);
         bool ok = true;
         for (int kb = 0; kb < C::KSTEPS; ++kb) {
-          if (!mbar_wait(&full[s], ph, abort)) {
+          if (!mbar_wait(&full[s], ph, abort) || (C::RAW && !mbar_wait(&cvt[s], ph, abort))) {
             ok = false;
             break;
           }
@@ -290,6 +309,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_wait(drain, 0, &never);
       }
     }
+  } else if (warp >= 2 + C::EPI_WARPS) {
+    // ---- (RAW) converters: split each landed K slice of x into hi / lo planes
+    if constexpr (C::RAW) {
+      const int ct = threadIdx.x - 32 * (2 + C::EPI_WARPS);  // 0 .. 127
+      constexpr int Q4 = C::XB / 16;                         // float4 per plane slice
+      int s = 0;
+      uint32_t ph = 0;
+      bool go = true;
+      for (long t = blockIdx.x; go && t < ntiles; t += gridDim.x) {
+        for (int kb = 0; kb < C::KSTEPS; ++kb) {
+          // warp-uniform: every lane of the warp takes the same exit
+          const bool ok = !*abort && mbar_wait(&full[s], ph, abort);
+          if (!__all_sync(0xffffffffu, ok)) {
+            go = false;
+            break;
+          }
+          unsigned char* st = base + s * C::STAGE_BYTES;
+          const float4* raw = reinterpret_cast<const float4*>(st + C::RAWOFF);
+          float4* spl = reinterpret_cast<float4*>(st);
+          for (int i = ct; i < C::NPX * Q4; i += 32 * C::CVT_WARPS) {
+            const int pl = i / Q4, o = i - pl * Q4;
+            const float4 v = raw[i];
+            float4 hi;
+            hi.x = tf32_hi(v.x);
+            hi.y = tf32_hi(v.y);
+            hi.z = tf32_hi(v.z);
+            hi.w = tf32_hi(v.w);
+            spl[(2 * pl) * Q4 + o] = hi;
+            spl[(2 * pl + 1) * Q4 + o] = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&cvt[s]);
+          if (++s == C::STAGES) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+      }
+    }
   } else {
     // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) ... + 31, i.e. output rows, and
     // the accumulator slots of its parity (w - 2) / 4
@@ -308,8 +367,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const uint32_t acc = tmem + (uint32_t)(bi * C::ACC) + ((uint32_t)(32 * q) << 16);
       const int gr = 128 * h + m;  // output row
-      float* on = p.out_n ? p.out_n + (size_t)b * C::NPL * kPlane : nullptr;
-      float* ot = p.out_t ? p.out_t + (size_t)b * C::NPL * kPlane : nullptr;
+      float* on = p.out_n ? p.out_n + (size_t)b * (p.plain_n ? C::NPX : C::NPL) * kPlane : nullptr;
+      float* ot = p.out_t ? p.out_t + (size_t)b * (p.plain_t ? C::NPX : C::NPL) * kPlane : nullptr;
       for (int slot = half; slot < C::TN / 16; slot += 2) {
         const int n0 = 16 * slot_block<ROT, C::NCG>(p.round, cg, slot);  // output column
         float vr[16], vi[16];
@@ -321,7 +380,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           vr[j] = p.alpha * vr[j] + ((gr == n0 + j) ? p.beta : 0.f);
           if constexpr (CPLX) vi[j] = ci * vi[j];
         }
-        if (on) {
+        if (on && p.plain_n) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int off = ((n0 / 4 + c) * 256 + gr) * 4;
+            *reinterpret_cast<float4*>(on + off) = make_float4(vr[4 * c], vr[4 * c + 1], vr[4 * c + 2], vr[4 * c + 3]);
+            if constexpr (CPLX)
+              *reinterpret_cast<float4*>(on + kPlane + off) =
+                  make_float4(vi[4 * c], vi[4 * c + 1], vi[4 * c + 2], vi[4 * c + 3]);
+          }
+        } else if (on) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const int off = ((n0 / 4 + c) * 256 + gr) * 4;
@@ -355,14 +423,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           // columns n0 .. n0 + 15; in D^T's KC4 layout a 4-row chunk of one column is one float4,
           // and the 16 columns of a chunk are 256 contiguous bytes, so each half-warp stores one
           // chunk row in one contiguous segment.
+          // plain: parts re (, im); split: parts re hi, re lo (, im hi, im lo)
           const int gr0 = 128 * h + 32 * q;
+          const int nparts = p.plain_t ? C::NPX : C::NPL;
 #pragma unroll
-          for (int part = 0; part < (CPLX ? 4 : 2); ++part) {
-            const float* v = (part < 2) ? vr : vi;
+          for (int part = 0; part < C::NPL; ++part) {
+            if (part >= nparts) break;
+            const bool im = p.plain_t ? part == 1 : part >= 2;
+            const float* v = im ? vi : vr;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const float hv = tf32_hi(v[j]);
-              tile_st[lane * 17 + j] = (part & 1) ? v[j] - hv : hv;
+              tile_st[lane * 17 + j] = p.plain_t ? v[j] : ((part & 1) ? v[j] - hv : hv);
             }
             __syncwarp();
 #pragma unroll
@@ -439,7 +511,8 @@ cudaError_t launch(const TcGemm& g, cudaStream_t s) {
     attr = true;
   }
   CUtensorMap mx, my;
-  if (!make_map(&mx, g.x, g.batch * C::NPL, 128) || !make_map(&my, g.y, g.batch * C::NPL, C::YR))
+  if (!make_map(&mx, g.x, g.batch * (C::RAW ? C::NPX : C::NPL), 128) ||
+      !make_map(&my, g.y, g.batch * C::NPL, C::YR))
     return cudaErrorInvalidValue;
   TcParams p;
   p.batch = g.batch;
@@ -448,6 +521,8 @@ cudaError_t launch(const TcGemm& g, cudaStream_t s) {
   p.round = g.round;
   p.conj_out = g.conj_out;
   p.withhold = g.withhold_loads;
+  p.plain_n = g.plain_n;
+  p.plain_t = g.plain_t;
   p.alpha = g.alpha;
   p.beta = g.beta;
   p.out_n = g.out_n;
@@ -455,7 +530,7 @@ cudaError_t launch(const TcGemm& g, cudaStream_t s) {
   p.err = g.err;
   const long tiles = 2L * C::NCG * g.batch;
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-  k_tcgemm<CPLX, ROT><<<grid, kThreads, C::SMEM, s>>>(mx, my, p);
+  k_tcgemm<CPLX, ROT><<<grid, C::THREADS, C::SMEM, s>>>(mx, my, p);
   return cudaGetLastError();
 }
 

@@ -14,8 +14,10 @@
 //      (Daleckii-Krein, see dk_stop in ve_device.cuh), and the rotations Q
 //   5. V2 = V1 Q (kept for the next sweep),  Y = V2 M V2^H
 // Steps 1-3 and 5 are seven batched tensor-core products; only step 4 runs on the SIMT pipes.
-// Every matrix is held "split" (hi = tf32 part, lo = remainder) in the KC4 layout of
-// ve_tcgemm.cu.
+// Matrices are held "split" (hi = tf32 part, lo = remainder) in the KC4 layout of ve_tcgemm.cu,
+// except the block-Jacobi operands A, W^T and V1, which the rotation products read and write
+// whole every round: those are plain float32 planes (re; re, im) in the same layout, split on
+// load inside the rotation kernel -- half the bytes.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,13 +65,13 @@ struct JShape {
 };
 
 // Step 4: one CTA of 512 threads per matrix, the matrix and its rotations staged in a per-CTA
-// slice of a global workspace (L2-resident).  In: A (split, KC4).  Out: M (split, KC4) and Q^T.
+// slice of a global workspace (L2-resident).  In: A (plain, KC4).  Out: M (split, KC4) and Q^T.
 template <bool CPLX>
 __global__ void __launch_bounds__(kNT, 1)
     k_tc_jacobi(const float* __restrict__ Ain, float* __restrict__ Mout, float* __restrict__ Qt, long count,
                 unsigned char* ws, unsigned long long* stats) {
   using S = JShape<CPLX>;
-  constexpr int NPL = CPLX ? 4 : 2;
+  constexpr int NPL = CPLX ? 4 : 2, NPX = CPLX ? 2 : 1;
   unsigned char* base = ws + (size_t)blockIdx.x * S::bytes;
   float* Ar = reinterpret_cast<float*>(base);
   float* Vr = reinterpret_cast<float*>(base + S::MAT);
@@ -79,25 +81,23 @@ __global__ void __launch_bounds__(kNT, 1)
   float* red = cs + 2 * kN;
   const int tid = threadIdx.x;
   for (long b = blockIdx.x; b < count; b += gridDim.x) {
-    const float* A = Ain + (size_t)b * NPL * kPl;
-    // load hi + lo (one float4 chunk of a row per thread and step: coalesced)
+    const float* A = Ain + (size_t)b * NPX * kPl;
+    // load (plain planes; one float4 chunk of a row per thread and step: coalesced)
     for (int q = tid; q < kPl / 4; q += kNT) {
       const int r = q % kN, k0 = (q / kN) * 4;
       const float4 h = *reinterpret_cast<const float4*>(A + 4 * q);
-      const float4 l = *reinterpret_cast<const float4*>(A + kPl + 4 * q);
       float* row = Ar + r * kLD + k0;
-      row[0] = h.x + l.x;
-      row[1] = h.y + l.y;
-      row[2] = h.z + l.z;
-      row[3] = h.w + l.w;
+      row[0] = h.x;
+      row[1] = h.y;
+      row[2] = h.z;
+      row[3] = h.w;
       if constexpr (CPLX) {
-        const float4 hi2 = *reinterpret_cast<const float4*>(A + 2 * kPl + 4 * q);
-        const float4 lo2 = *reinterpret_cast<const float4*>(A + 3 * kPl + 4 * q);
+        const float4 h2 = *reinterpret_cast<const float4*>(A + kPl + 4 * q);
         float* ri = Ai + r * kLD + k0;
-        ri[0] = hi2.x + lo2.x;
-        ri[1] = hi2.y + lo2.y;
-        ri[2] = hi2.z + lo2.z;
-        ri[3] = hi2.w + lo2.w;
+        ri[0] = h2.x;
+        ri[1] = h2.y;
+        ri[2] = h2.z;
+        ri[3] = h2.w;
       }
     }
     __syncthreads();
@@ -197,14 +197,14 @@ struct SubShape {
 
 __device__ __forceinline__ int kc4i(int r, int k) { return ((k >> 2) * kN + r) * 4 + (k & 3); }
 
-// ||A_b||_F^2 of every matrix (hi + lo), one CTA per matrix, fixed summation order.
-__global__ void __launch_bounds__(256) k_fro2(const float* __restrict__ A, int npl, float* __restrict__ out) {
+// ||A_b||_F^2 of every matrix (npx plain planes), one CTA per matrix, fixed summation order.
+__global__ void __launch_bounds__(256) k_fro2(const float* __restrict__ A, int npx, float* __restrict__ out) {
   __shared__ float red[8];
-  const float* a = A + (size_t)blockIdx.x * npl * kPl;
+  const float* a = A + (size_t)blockIdx.x * npx * kPl;
   float s = 0.f;
-  for (int pl = 0; pl < npl; pl += 2)
+  for (int pl = 0; pl < npx; ++pl)
     for (int e = threadIdx.x; e < kPl; e += 256) {
-      const float v = a[pl * kPl + e] + a[(pl + 1) * kPl + e];
+      const float v = a[pl * kPl + e];
       s = fmaf(v, v, s);
     }
   s = gsum<256>(s, red);
@@ -235,12 +235,12 @@ __global__ void __launch_bounds__(32 * kSubWarps)
     int bp, bq;
     rr_pair(kNB, round, k, bp, bq);
     auto g = [&](int t) { return t < kBS ? bp * kBS + t : bq * kBS + (t - kBS); };
-    const float* a = A + (size_t)b * NPL * kPl;
+    const float* a = A + (size_t)b * (NPL / 2) * kPl;  // plain: re (, im)
     for (int e = lane; e < kSub * kSub; e += 32) {
       const int i = e / kSub, j = e % kSub;
       const int o = kc4i(g(i), g(j));
-      Sr[i * kSLD + j] = a[o] + a[kPl + o];
-      if constexpr (CPLX) Si[i * kSLD + j] = a[2 * kPl + o] + a[3 * kPl + o];
+      Sr[i * kSLD + j] = a[o];
+      if constexpr (CPLX) Si[i * kSLD + j] = a[kPl + o];
     }
     __syncwarp();
     // (S + S^H) / 2
@@ -293,6 +293,24 @@ __global__ void __launch_bounds__(32 * kSubWarps)
   }
 }
 
+// Plain -> split: every float32 of `count` matrices of npx plain planes (KC4) becomes its hi / lo
+// pair in 2 npx planes.
+__global__ void k_tc_split(const float* __restrict__ in, float* __restrict__ out, long count, int npx) {
+  const long total = count * npx * (long)(kPl / 4);
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+    const long mp = q / (kPl / 4);  // matrix * npx + plane
+    const int c = (int)(q % (kPl / 4));
+    const float4 v = reinterpret_cast<const float4*>(in)[q];
+    float hv[4] = {v.x, v.y, v.z, v.w};
+    float4 hi, lo;
+    split4(hv, hi, lo);
+    const long mat = mp / npx, pl = mp % npx;
+    float* o = out + ((size_t)mat * 2 * npx + 2 * pl) * kPl + (size_t)c * 4;
+    *reinterpret_cast<float4*>(o) = hi;
+    *reinterpret_cast<float4*>(o + kPl) = lo;
+  }
+}
+
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
@@ -333,7 +351,7 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   auto gemm = [&](const float* x, int cx, const float* y, int cy, float alpha, float beta, float* on,
-                  float* ot) {
+                  float* ot, int plain_n = 0) {
     TcGemm g;
     g.x = x;
     g.y = y;
@@ -345,17 +363,20 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
     g.beta = beta;
     g.out_n = on;
     g.out_t = ot;
+    g.plain_n = plain_n;
     g.err = w.err;
     return tc_gemm256(g, s);
   };
+  // The block-Jacobi operands A, W^T (as B = A R) and V1 are kept plain (float32 planes, half the
+  // bytes of the split form): the rotation products read and write them whole every round.
   // 1. T = 1.5 I - 0.5 V^H V   (V^H V)_ij = sum_k conj(Vt_ik) Vt_jk
   if ((e = gemm(w.Vt, 1, w.Vt, 0, -0.5f, 1.5f, w.T, nullptr)) != cudaSuccess) return e;
-  // 2. V1 = V T: the right factor enters as T^T = conj(T)
-  if ((e = gemm(w.V, 0, w.T, 1, 1.f, 0.f, w.V1, w.V1t)) != cudaSuccess) return e;
-  // 3. W = C V1 (kept as W^T), then A = V1^H W into T's storage
+  // 2. V1 = V T (plain) and V1^T (split): the right factor enters as T^T = conj(T)
+  if ((e = gemm(w.V, 0, w.T, 1, 1.f, 0.f, w.V1, w.V1t, 1)) != cudaSuccess) return e;
+  // 3. W = C V1 (kept as W^T), then A = V1^H W into T's storage (plain)
   if ((e = gemm(w.C, 0, w.V1t, 0, 1.f, 0.f, nullptr, w.Wt)) != cudaSuccess) return e;
   float* A = w.T;
-  if ((e = gemm(w.V1t, 1, w.Wt, 0, 1.f, 0.f, A, nullptr)) != cudaSuccess) return e;
+  if ((e = gemm(w.V1t, 1, w.Wt, 0, 1.f, 0.f, A, nullptr, 1)) != cudaSuccess) return e;
   // block-Jacobi sweeps: R^T in Qt's storage, A R kept transposed in Wt
   {
     const size_t smem = w.cplx ? SubShape<true>::bytes : SubShape<false>::bytes;
@@ -370,7 +391,7 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
     const long ctas = (items + kSubWarps - 1) / kSubWarps;
     const int sgrid = (int)(ctas < 8L * big_grid() ? ctas : 8L * big_grid());
     float* fro2 = reinterpret_cast<float*>(w.M);  // M is free until the polish
-    k_fro2<<<(unsigned)count, 256, 0, s>>>(A, w.cplx ? 4 : 2, fro2);
+    k_fro2<<<(unsigned)count, 256, 0, s>>>(A, w.cplx ? 2 : 1, fro2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Two block sweeps, each sub-problem one Jacobi sweep (an inexact block solve: the polish
     // below completes the eigensolve to the full tolerance).  Measured in steady state on the
@@ -388,7 +409,7 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // B = A R (kept transposed in Wt); A <- R^H B written as (B^H R)^H; V1 <- V1 R.  All
         // three multiply by the block rotation R on the right (tc_rot256: its nonzero blocks
-        // only).
+        // only), plain in and plain out.
         auto rot = [&](const float* x, int cx, float* on, float* ot, int co) {
           TcGemm g;
           g.x = x;
@@ -398,6 +419,8 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
           g.conj_x = cx;
           g.out_n = on;
           g.out_t = ot;
+          g.plain_n = 1;
+          g.plain_t = 1;
           g.conj_out = co;
           g.round = r;
           g.err = w.err;
@@ -417,8 +440,15 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
   else
     k_tc_jacobi<false><<<grid, kNT, 0, s>>>(A, w.M, w.Qt, count, w.jws, stats);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // 5. V2 = V1 Q (the stored eigenvectors), Z = V2 M into C, Y = Z V2^H into Wt
-  if ((e = gemm(w.V1, 0, w.Qt, 0, 1.f, 0.f, w.V, w.Vt)) != cudaSuccess) return e;
+  // 5. V2 = V1 Q (the stored eigenvectors; V1 split into V1t's storage first), Z = V2 M into C,
+  // Y = Z V2^H into Wt
+  {
+    const long q = count * (npl / 2) * (long)(kPl / 4);
+    const int g2 = (int)((q + 255) / 256 < 8192 ? (q + 255) / 256 : 8192);
+    k_tc_split<<<g2, 256, 0, s>>>(w.V1, w.V1t, count, npl / 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = gemm(w.V1t, 0, w.Qt, 0, 1.f, 0.f, w.V, w.Vt)) != cudaSuccess) return e;
   if ((e = gemm(w.V, 0, w.M, 1, 1.f, 0.f, w.C, nullptr)) != cudaSuccess) return e;
   return gemm(w.C, 0, w.V, 1, 1.f, 0.f, w.Wt, nullptr);
 }
