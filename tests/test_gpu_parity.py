@@ -521,18 +521,20 @@ def test_mixed_sweeps_track_the_oracle(ve, lattice, cluster):
         ve.ve_destroy(h)
 
 
-def test_full_size_4spin_chain_mixed_matches_oracle(ve):
-    """The 4-spin-cluster benchmark chain itself (4096 spins, 1024 clusters, D = 256: 513
-    canonical wavevector blocks and 512 pair blocks per projection batch) in mixed precision, the
-    tensor-core path as the benchmark runs it (captured sweep graph after the first sweep), two
-    sweeps from the cold start against the float64 oracle over the whole state: within twice the
-    per-sweep float32 bound of the test above, and the certificate within 1e-3 per spin."""
-    lattice, cluster = (4096,), (4,)
+@pytest.mark.parametrize("lattice,cluster,x", [((4096,), (4,), 1.0), ((64, 64), (2, 2), 3.0)])
+def test_full_size_4spin_chain_mixed_matches_oracle(ve, lattice, cluster, x):
+    """The two 4-spin-cluster benchmark workloads themselves -- the 4096-spin chain and the 2-D
+    64 x 64 lattice in 2 x 2 clusters (1024 clusters each, D = 256: 513 / 514 canonical wavevector
+    blocks and 512 pair blocks per projection batch) -- in mixed precision, the tensor-core path
+    as the benchmark runs it (captured sweep graph after the first sweep), two sweeps from the
+    cold start against the float64 oracle over the whole state: within twice the per-sweep
+    float32 bound of the test above, and the certificate within 1e-3 per spin."""
+    dim = len(lattice)
     vo.set_threads(os.cpu_count() or 1)
     try:
-        pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, 1.0, 1)))
+        pb = vo.Problem(mo.cluster_model(lattice, cluster, *mo.tfim_terms(1.0, x, dim)))
         st = vo.initial_state(pb)
-        h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(1, 1.0, 1.0),
+        h = ve.ve_create(lattice, cluster, ve.ve_ham_tfim(dim, 1.0, x),
                          ve.ve_default_options(precision=1))
         try:
             ve.ve_iterate(h, 2, 0.0)
