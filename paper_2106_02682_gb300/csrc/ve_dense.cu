@@ -21,9 +21,9 @@
 // nearby matrices), W = Y V by one GEMM.  Stopping: after a sweep whose rotated blocks satisfy
 // 2 sum a_pq^2 <= (n u)^2 ||Y||_F^2 (the rule of the batched eigensolvers).  Then
 // lambda_i = v_i.w_i and X = V diag(max(lambda, 0)) V^T by a GEMM.
-// Early stop (allow_dk): once a sweep's rotations were small (2 sum a_pq^2 <= 1e-10 ||Y||_F^2,
-// so quadratic convergence has left A = V^T Y V within ~1e-10 of diagonal), A is formed by one
-// GEMM and its off-diagonal part E checked: ||E||_F^2 <= (n u)^2 ||A||_F^2 means converged
+// Early stop (allow_dk): once a sweep's rotations were small (2 sum a_pq^2 <= 1e-6 ||Y||_F^2,
+// so quadratic convergence has left A = V^T Y V within ~1e-6 ||Y|| / gap of diagonal), A is
+// formed by one GEMM and its off-diagonal part E checked: ||E||_F^2 <= (n u)^2 ||A||_F^2 means converged
 // without the confirming sweep; ||E||_F^4 <= (n u)^2 ||A||_F^2 d^2 and ||E||_F <= d / 4, d the
 // distance of diag(A) from zero, means the first-order expansion f(A) = f(Lambda) + L o E
 // (Daleckii-Krein, f = max(., 0), L the divided differences) is as accurate as the exact rule,
@@ -39,8 +39,11 @@ namespace ve {
 namespace {
 
 constexpr int RT = 128;  // threads of a round CTA
-// A sweep whose rotations summed below this fraction of ||Y||_F^2 triggers the explicit check.
-constexpr double kDkTrigger = 1e-10;
+// A sweep whose rotations summed below this fraction of ||Y||_F^2 triggers the explicit check
+// (one GEMM and one reduction: cheap against a sweep of n - 1 round launches, so it is tried as
+// soon as one more sweep could leave A within ~1e-12 of diagonal; measured on the 20-site
+// fermion rings, 1e-6 instead of 1e-10 took the float64 sweeps per X step from 3.55 to 3.1).
+constexpr double kDkTrigger = 1e-6;
 
 template <int EPT>
 __global__ void __launch_bounds__(RT) k_dense_round(double* __restrict__ Vt, double* __restrict__ Wt,
