@@ -204,8 +204,10 @@ cudaError_t tc_gemm256(const TcGemm& g, cudaStream_t s);
 // ordering (rr_pair(TC_BJ_NB, round, k)), TC_BJ_NB - 1 rounds a sweep.
 constexpr int TC_BJ_BS = 16, TC_BJ_NB = 256 / TC_BJ_BS;
 // x_b R_b for a block rotation R of round g.round, R nonzero only on each pair's 2 TC_BJ_BS square
-// block.  g.y holds R^T (split); only its pairs' row slices are read, and each output column block
-// accumulates over its pair's indices: 2 TC_BJ_BS / 256 of the products of tc_gemm256.  g.x is
+// block.  g.y holds R compactly (split): per matrix NPL planes of 256 rows x 2 TC_BJ_BS columns in
+// the KC4 layout, row 2 TC_BJ_BS j + c and column a holding R[I_j[a]][I_j[c]] for pair j's index
+// list I_j (its block p, then block q); each output column block accumulates over its pair's
+// indices: 2 TC_BJ_BS / 256 of the products of tc_gemm256.  g.x is
 // plain (split inside the kernel: the rotations move their whole operand for 1/8 of a product's
 // MMAs, so its bytes are the cost).
 cudaError_t tc_rot256(const TcGemm& g, cudaStream_t s);

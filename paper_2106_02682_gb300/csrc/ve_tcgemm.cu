@@ -36,8 +36,10 @@ namespace {
 
 using namespace tc;
 
-// ROT: the right factor is a block rotation R (see tc_rot256): only the TC_BJ_BS-row slices of
-// y = R^T that hold a pair's blocks are loaded, two per stage; a stage's K slice is one block.
+// ROT: the right factor is a block rotation R (see tc_rot256), stored compactly: per pair its
+// 32 x 32 block (rows: the pair's 32 output columns, K: the pair's 32 indices).  A stage's K slice
+// is one block of the pair, and one 32-row box per plane feeds N = 32 MMAs into the accumulator
+// slots of both output blocks.
 //
 // A tile is (matrix, 128-row half, column group): NCG column groups of TN output columns.  Its
 // accumulator (re, and im when complex) takes ACC tensor-memory columns, and NBUF = 512 / ACC
@@ -55,9 +57,9 @@ struct TcCfg {
   static constexpr bool RAW = ROT;                    // x plain, split in the kernel
   static constexpr int KS = 16;                       // K elements per stage
   static constexpr int XB = 128 * KS * 4;             // bytes of one X plane slice (128 rows)
-  static constexpr int YR = ROT ? TC_BJ_BS : 256;     // rows of one Y plane slice
-  static constexpr int YB = YR * KS * 4;              // bytes of one Y plane slice
-  static constexpr int NYS = ROT ? 2 : 1;             // Y slices per plane and stage
+  static constexpr int YR = ROT ? 2 * TC_BJ_BS : 256;  // rows of one Y plane slice
+  static constexpr int YB = YR * KS * 4;               // bytes of one Y plane slice
+  static constexpr int NYS = 1;                        // Y slices per plane and stage
   static constexpr int RAWOFF = NPL * (XB + NYS * YB);  // raw x within a stage
   static constexpr int STAGE_BYTES = RAWOFF + (RAW ? NPX * XB : 0);
   static constexpr int TX_BYTES = (RAW ? NPX : NPL) * XB + NPL * NYS * YB;  // loaded by the TMA
@@ -92,9 +94,6 @@ struct TcParams {
   float* out_t;
   int* err;
 };
-
-// Element (r, k) of a KC4 plane.
-__device__ __forceinline__ int kc4(int r, int k) { return ((k >> 2) * 256 + r) * 4 + (k & 3); }
 
 // Pair k of round r of the circle ordering of the TC_BJ_NB column blocks (p < q), as rr_pair.
 __device__ __forceinline__ void block_pair(int r, int k, int& p, int& q) {
@@ -206,11 +205,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             if constexpr (!C::RAW)
               tma_load_4d(st + pl * C::XB, &mx, &full[s], 0, 128 * h, kslice * (C::KS / 4), b * C::NPL + pl);
             if constexpr (ROT) {
-              // the rows of R^T (columns of R) in the pair's two blocks
-              tma_load_4d(st + C::NPL * C::XB + (0 * C::NPL + pl) * C::YB, &my, &full[s], 0,
-                          TC_BJ_BS * bp, kslice * (C::KS / 4), b * C::NPL + pl);
-              tma_load_4d(st + C::NPL * C::XB + (1 * C::NPL + pl) * C::YB, &my, &full[s], 0,
-                          TC_BJ_BS * bq, kslice * (C::KS / 4), b * C::NPL + pl);
+              // the pair's compact 32 x 32 block: its 32 rows, the K half of this stage's block
+              const int jg = cg * (TC_BJ_NB / 2 / C::NCG) + (kb >> 1);
+              tma_load_4d(st + C::NPL * C::XB + pl * C::YB, &my, &full[s], 0, 2 * TC_BJ_BS * jg,
+                          (kb & 1) * (C::KS / 4), b * C::NPL + pl);
             } else {
               tma_load_4d(st + C::NPL * C::XB + pl * C::YB, &my, &full[s], 0, 0, kslice * (C::KS / 4),
                           b * C::NPL + pl);
@@ -256,13 +254,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           tc_fence_after();
           const uint32_t st = smem_u32(base + s * C::STAGE_BYTES);
           const uint32_t xs = st, ys0 = st + C::NPL * C::XB;
-          // ROT: the stage's K slice feeds the accumulator slots of both blocks of its pair, each
-          // accumulated only over the pair's 2 stages (R is zero elsewhere): N = TC_BJ_BS
+          // ROT: the stage's K slice feeds the accumulator slots of both blocks of its pair (N =
+          // 2 TC_BJ_BS, adjacent slots), accumulated only over the pair's 2 stages (R is zero
+          // elsewhere)
 #pragma unroll
           for (int cb = 0; cb < C::NYS; ++cb) {
             const uint32_t ys = ys0 + cb * C::NPL * C::YB;
-            const uint32_t c0 = ROT ? (uint32_t)TC_BJ_BS * (uint32_t)(2 * (kb >> 1) + cb) : 0u;
-            constexpr int NN = ROT ? TC_BJ_BS : 256;
+            const uint32_t c0 = ROT ? (uint32_t)TC_BJ_BS * (uint32_t)(2 * (kb >> 1)) : 0u;
+            constexpr int NN = ROT ? 2 * TC_BJ_BS : 256;
 #pragma unroll
             for (int ks = 0; ks < C::KS / 8; ++ks) {
               auto mma = [&](int xp, int yp, uint32_t col, int neg, bool first) {
@@ -477,12 +476,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Tensor map over `planes` KC4 planes at `ptr`: dims (k % 4, r, k / 4, plane), box (4, rows, 4, 1).
-bool make_map(CUtensorMap* map, const float* ptr, long planes, int rows) {
+// Tensor map over `planes` KC4 planes of 256 rows x kdim columns at `ptr`: dims (k % 4, r, k / 4,
+// plane), box (4, rows, 4, 1).  kdim = 256 for the matrices, 32 for the compact rotations.
+bool make_map(CUtensorMap* map, const float* ptr, long planes, int rows, int kdim = 256) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[4] = {4, 256, 64, (cuuint64_t)planes};
-  cuuint64_t strides[3] = {16, 256 * 16, (cuuint64_t)kPlane * 4};
+  cuuint64_t dims[4] = {4, 256, (cuuint64_t)(kdim / 4), (cuuint64_t)planes};
+  cuuint64_t strides[3] = {16, 256 * 16, (cuuint64_t)256 * kdim * 4};
   cuuint32_t box[4] = {4, (cuuint32_t)rows, 4, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(ptr), dims, strides, box, es,
@@ -512,7 +512,7 @@ cudaError_t launch(const TcGemm& g, cudaStream_t s) {
   }
   CUtensorMap mx, my;
   if (!make_map(&mx, g.x, g.batch * (C::RAW ? C::NPX : C::NPL), 128) ||
-      !make_map(&my, g.y, g.batch * C::NPL, C::YR))
+      !make_map(&my, g.y, g.batch * C::NPL, C::YR, ROT ? 2 * TC_BJ_BS : 256))
     return cudaErrorInvalidValue;
   TcParams p;
   p.batch = g.batch;

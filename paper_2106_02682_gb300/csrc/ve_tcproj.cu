@@ -184,9 +184,10 @@ __global__ void __launch_bounds__(kNT, 1)
 // (I, J) the 32 x 32 principal block A[I u J, I u J] is diagonalised exactly by one warp in shared
 // memory (k_bj_sub), its eigenvectors U placed in the round's rotation R (R[I u J, I u J] = U,
 // zero elsewhere), and A <- R^H A R, V <- V R are three tensor-core products that touch only
-// R's nonzero blocks (tc_rot256), so only those blocks of R^T are ever written.  A sweep of rounds annihilates every off-diagonal
+// R's nonzero blocks (tc_rot256), which are stored compactly (one 32 x 32 block per pair).  A sweep of rounds annihilates every off-diagonal
 // block once; like scalar Jacobi it converges quadratically.
 constexpr int kBS = TC_BJ_BS, kNB = TC_BJ_NB, kSub = 2 * kBS, kSLD = kSub + 1, kSubWarps = 4;
+constexpr int kRc = kN * kSub;  // floats of one plane of a compact rotation (256 rows x 32 K)
 
 template <bool CPLX>
 struct SubShape {
@@ -266,27 +267,28 @@ __global__ void __launch_bounds__(32 * kSubWarps)
                                                max_inner);
     else
       jacobi_sym<float, kSub, kSLD, 32, true>(Sr, Ur, cs, red, lane, nullptr, nullptr, floor2, max_inner);
-    // R^T on the pair's index set: R^T[g(j)][g(t)] = U[t][j].  tc_rot256 reads R^T only there
-    // (the rows of the pair's column blocks at the pair's K slices), so the zeros elsewhere are
-    // never written.  A lane writes one 4-index chunk of one row as a float4.
-    float* rt = Rt + (size_t)b * NPL * kPl;
+    // The round's rotation, compact: per matrix NPL split planes of 256 rows x 32 K (KC4), row
+    // 32 k + c and K index a holding U[a][c] (pair-local indices, block bp then block bq): the
+    // rotation products read each pair's 32 x 32 block as one box.  A lane writes one 4-index
+    // chunk of one row as a float4.
+    float* rc = Rt + (size_t)b * NPL * kRc;
     for (int e = lane; e < kSub * (kSub / 4); e += 32) {
-      const int j = e / (kSub / 4), tc = e % (kSub / 4);  // row g(j) of R^T, chunk g(4 tc)..+3
+      const int c = e / (kSub / 4), ch = e % (kSub / 4);  // row 32 k + c, K chunk 4 ch .. + 3
       float ur[4], ui[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        ur[u] = Ur[(4 * tc + u) * kSLD + j];
-        if constexpr (CPLX) ui[u] = Ui[(4 * tc + u) * kSLD + j];
+        ur[u] = Ur[(4 * ch + u) * kSLD + c];
+        if constexpr (CPLX) ui[u] = Ui[(4 * ch + u) * kSLD + c];
       }
-      const int o = ((g(4 * tc) >> 2) * kN + g(j)) * 4;
+      const int o = (ch * kN + kSub * k + c) * 4;
       float4 hi, lo;
       split4(ur, hi, lo);
-      *reinterpret_cast<float4*>(rt + o) = hi;
-      *reinterpret_cast<float4*>(rt + kPl + o) = lo;
+      *reinterpret_cast<float4*>(rc + o) = hi;
+      *reinterpret_cast<float4*>(rc + kRc + o) = lo;
       if constexpr (CPLX) {
         split4(ui, hi, lo);
-        *reinterpret_cast<float4*>(rt + 2 * kPl + o) = hi;
-        *reinterpret_cast<float4*>(rt + 3 * kPl + o) = lo;
+        *reinterpret_cast<float4*>(rc + 2 * kRc + o) = hi;
+        *reinterpret_cast<float4*>(rc + 3 * kRc + o) = lo;
       }
     }
     __syncwarp();
@@ -377,7 +379,7 @@ cudaError_t tc_project256(TcProjWs& w, long count, bool warm, unsigned long long
   if ((e = gemm(w.C, 0, w.V1t, 0, 1.f, 0.f, nullptr, w.Wt)) != cudaSuccess) return e;
   float* A = w.T;
   if ((e = gemm(w.V1t, 1, w.Wt, 0, 1.f, 0.f, A, nullptr, 1)) != cudaSuccess) return e;
-  // block-Jacobi sweeps: R^T in Qt's storage, A R kept transposed in Wt
+  // block-Jacobi sweeps: the compact rotations in Qt's storage, A R kept transposed in Wt
   {
     const size_t smem = w.cplx ? SubShape<true>::bytes : SubShape<false>::bytes;
     static bool attr[2] = {false, false};
