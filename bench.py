@@ -347,6 +347,12 @@ def run_ours(args):
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
         roof["kernel"] = dom
+        if D == 256 and prec == 1:
+            roof["note"] = ("stage-level: the float32 projections of this stage run as tensor-core "
+                            "products (tcgen05, HBM- and chain-bound block rotations) plus SIMT "
+                            "block solves; frac counts the nominal eigensolve flops against the "
+                            "FP32 SIMT rate. Per-kernel bounds: profiles/"
+                            "launches_tfim1d_L4_N1024_mixed.md")
         roof["ms_per_launch"] = ms_launch
         rec = ncu_record(dom, args.workload, args.precision)
         roof["traffic"] = rec.get("dram_bytes_per_launch") if rec else None
